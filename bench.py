@@ -1,0 +1,391 @@
+"""Benchmark: Mrays/s of the Schwarzschild renderer on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--form mixed|fp32|fp64] [--size 4096]
+
+One step = one bh_render of the whole hot path over the workload: pinhole
+camera rays, orbital-plane reduction, Dormand-Prince 5(4) with event location
+(disk, spheres, capture, escape), shading and the SoA stores.  The default
+workload is the 4096 x 4096 mixed-precision frame (r_obs = 50M, inclination
+75 deg, disk [6M, 30M], 8 seeded spheres, FP32 stepping with FP64 for the
+periastron reset and for |b - 3 sqrt(3) M| < 0.05M).  Rank 0 prints one JSON
+line.  `--impl reference` times the CPU oracle instead (the FP64 plain
+renderer on the host cores, a bounded pixel sample per step).
+
+Multi-GPU: the path has no exchange step; N ranks render N independent
+frames (replicas, weak scaling) and the value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2507_16165_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Mrays/s at 4096^2 (FP64 / FP32 / MLP surrogate) at stated exit-dir error"
+UNIT = "Mrays/s"
+# FP32 FMA-pipe operations of one attempted Dormand-Prince step, counted from
+# dp5_attempt and step_factor in csrc/tracer.cuh: 26 MUL + 59 FMA in the
+# stages, error norm and scales, plus 4 in the step controller; an FMA counts
+# as two floating-point operations.
+FLOP_PER_STEP = 2 * 59 + 26 + 4
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9}
+KERNELS_PER_RENDER = {"mixed": 3, "fp32": 2, "fp64": 2}
+
+
+def workload(form: str, size: int):
+    return W.config3(size, form)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_16165_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def profile_traffic(form: str) -> float | None:
+    """DRAM bytes per launch of the coherent kernel from a committed ncu
+    summary, or None when absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(form)
+    if not e or e.get("source_sha") != source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds: float = 10.0, seed: int = 0) -> dict:
+    """The CPU oracle, as it stands, on a seeded random pixel sample of the
+    workload, with every host core (OpenMP).  Test infrastructure: this leg is
+    the only part of the GPU benchmark that runs the oracle."""
+    import numpy as np
+
+    import oracle
+    lib = oracle.load()
+    cores = oracle.threads(os.cpu_count() or 1, lib=lib)
+    cam = w.cameras[0]
+    rng = np.random.default_rng(seed)
+    o = oracle.opts(rtol=1e-10, atol=1e-10)
+
+    def run(n):
+        idx = rng.integers(0, cam.w * cam.h, n)
+        t0 = time.perf_counter()
+        oracle.render_pixels(w.scene, w.cameras, np.zeros(n, np.int32), idx % cam.w,
+                             idx // cam.w, o, nthreads=cores, lib=lib)
+        return time.perf_counter() - t0
+
+    probe = 1 << 14
+    dt = run(probe)
+    n = int(min(1 << 24, max(probe, probe * seconds / max(dt, 1e-6))))
+    dt = run(n)
+    return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded random pixels of the {cam.w}x{cam.h} frame, FP64 oracle "
+                      f"(rtol = atol = 1e-10), OpenMP dynamic schedule over the pixel list, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    """The CPU oracle timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    w = workload(args.form, args.size)
+    lib = oracle.load()
+    cores = oracle.threads(os.cpu_count() or 1, lib=lib)
+    cam = w.cameras[0]
+    rng = np.random.default_rng(1)
+    n = args.ref_pixels
+    o = oracle.opts(rtol=1e-10, atol=1e-10)
+
+    def step():
+        idx = rng.integers(0, cam.w * cam.h, n)
+        oracle.render_pixels(w.scene, w.cameras, np.zeros(n, np.int32), idx % cam.w,
+                             idx // cam.w, o, nthreads=cores, lib=lib)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name} (oracle on a {n}-pixel sample per step)",
+                   "rays_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} seeded random pixels per step of the {cam.w}x{cam.h} "
+                                   "frame, FP64 rtol = atol = 1e-10"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    import paper_2507_16165_gb300 as bh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            t = torch.ones(1, device="cuda")
+            dist.all_reduce(t)
+        torch.cuda.synchronize()
+
+    w = workload(args.form, args.size)
+    n = w.n_rays
+    sc = bh.Scene(w.scene)
+    cams = sc.cameras(w.cameras)
+    wv = [c.w for c in w.cameras]
+    hv = [c.h for c in w.cameras]
+    stream = torch.cuda.Stream()
+    f64 = args.form == "fp64"
+    dirs = torch.empty(2 * n, dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    flags = torch.empty(n, dtype=torch.int16, device="cuda")
+    rgba = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band)
+
+    def render():
+        bh.bh_render(sc.handle, cams, wv, hv, dirs, flags, rgba, opts)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            render()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms, steps32, steps_all = [], 0, 0
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)                 # L2 flush, outside the events
+                starts[k].record(stream)
+                render()
+                ends[k].record(stream)
+            st = bh.bh_render_stats(sc.handle)       # syncs the stream, outside the events
+            kernel_ms.append(st["kernel_ms"])
+            steps_all += st["steps"]
+            steps32 += st["steps"] - st["steps_fp64"]
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    bh.bh_scene_sync(sc.handle)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms * 1e-3) / 1e6
+
+    # roofline: the FP32 integrator kernels (coherent + long-ray passes)
+    int_ms = sum(km[0] + km[1] for km in kernel_ms)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    if f64:
+        achieved = None
+    else:
+        achieved = steps32 * FLOP_PER_STEP / (int_ms * 1e-3) / 1e12
+    roofline = {
+        "bound": "alu",
+        "achieved": achieved,
+        "peak": peak_tflops,
+        "unit": "TFLOP/s",
+        "frac": (achieved / peak_tflops) if achieved is not None else None,
+        "traffic": profile_traffic(args.form),
+        "kernel": "k_coherent + k_longrays (FP32 Dormand-Prince steps)",
+        "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+                       f"{sm_max:.0f} MHz (max SM clock)",
+        "algorithmic": f"{FLOP_PER_STEP} FLOP per attempted FP32 step x "
+                       f"{steps32 / args.steps:.0f} steps per frame",
+        "integrator_ms_per_step": int_ms / args.steps,
+    }
+
+    # end to end through the C-ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hd = torch.empty(2 * n, dtype=dirs.dtype, pin_memory=True)
+        hf = torch.empty(n, dtype=torch.int16, pin_memory=True)
+        hr = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        for _ in range(max(1, args.warmup)):
+            bh.bh_render_host(sc.handle, cams, wv, hv, hd, hf, hr, opts)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            bh.bh_render_host(sc.handle, cams, wv, hv, hd, hf, hr, opts)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        import ctypes
+        from paper_2507_16165_gb300 import _capi
+        e2e = {"value": world * n * args.steps / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": len(cams) * (ctypes.sizeof(_capi.bh_camera) + 8),
+               "d2h_bytes_per_step": n * (dirs.element_size() * 2 + 2 + 4)}
+
+    stats = bh.bh_render_stats(sc.handle)
+    sc.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None if (args.no_cpu or world > 1) else cpu_baseline(w, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "form": args.form, "rays_per_step": n,
+                   "size": f"{args.size}x{args.size}", "r_obs": 50.0, "inclination_deg": 75.0,
+                   "disk": [6.0, 30.0], "spheres": 8, "rtol": w.rtol, "atol": w.atol,
+                   "band": w.band, "stated_exit_dir_error_rad": STATED_ERROR[args.form],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written between timed steps (outside the events)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": KERNELS_PER_RENDER[args.form] * args.steps,
+        "clocks": clk.summary(),
+        "steps_per_ray": steps_all / args.steps / n,
+        "wall_s": t_wall,
+        "stats_last": {k: stats[k] for k in ("rays", "n_band", "n_long", "periastron", "n_capt",
+                                             "n_disk", "n_sphere", "n_esc")},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--form", choices=("mixed", "fp32", "fp64"), default="mixed")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-pixels", type=int, default=1 << 18)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

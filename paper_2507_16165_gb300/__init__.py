@@ -1,0 +1,200 @@
+"""GB300 Schwarzschild light-ray renderer: thin Python binding of libbh.so.
+
+The functions named bh_* mirror the C-ABI in include/bh.h one to one and only
+marshal arguments (torch tensors -> device pointers, Python numbers -> C
+structs).  All rendering runs in the CUDA kernels of libbh.so; importing this
+package does not load the library, the first bh_* call does, and it raises if
+the library has not been built.
+
+    import torch, paper_2507_16165_gb300 as bh
+    from paper_2507_16165_gb300 import workloads as W
+    w = W.config2(256, "fp32")
+    out = bh.render_workload(w)            # dict of torch CUDA tensors
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _capi
+from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # noqa: F401
+                    BH_FLAG_FP64, BH_FLAG_SPHERE, BH_FLAG_STEP_LIMIT, BH_FLAG_SURR,
+                    BH_MODE_FP32, BH_MODE_FP64, BH_MODE_MIXED, BH_MODE_SURROGATE, MODES,
+                    BHError, check)
+
+__all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
+           "bh_camera_set", "bh_render", "bh_render_host", "bh_scene_sync",
+           "bh_render_stats", "Scene", "render_opts", "render_workload"]
+
+
+def bh_version() -> int:
+    return int(_capi.lib().bh_version())
+
+
+def bh_last_error() -> str:
+    return _capi.lib().bh_last_error().decode(errors="replace")
+
+
+def scene_desc(scene) -> _capi.bh_scene_desc:
+    """C scene description from a workloads.Scene-like object."""
+    d = _capi.bh_scene_desc()
+    d.mass = float(scene.mass)
+    disk = getattr(scene, "disk", None)
+    d.disk_enabled = 1 if disk is not None else 0
+    if disk is not None:
+        d.disk_r_in, d.disk_r_out = float(disk[0]), float(disk[1])
+    sph = list(getattr(scene, "spheres", ()))
+    if len(sph) > _capi.BH_MAX_SPHERES:
+        raise ValueError("at most 8 spheres")
+    d.n_spheres = len(sph)
+    for k, s in enumerate(sph):
+        d.spheres[k].center[:] = [float(x) for x in s.center]
+        d.spheres[k].radius = float(s.radius)
+        d.spheres[k].albedo[:] = [float(x) for x in s.albedo]
+    d.sky_seed = int(scene.sky_seed)
+    d.ic = int(getattr(scene, "ic", 0))
+    return d
+
+
+def bh_scene_create(desc: _capi.bh_scene_desc) -> int:
+    h = ctypes.c_void_p()
+    check(_capi.lib().bh_scene_create(ctypes.byref(desc), ctypes.byref(h)), "bh_scene_create")
+    return h.value
+
+
+def bh_scene_destroy(handle: int) -> None:
+    if handle:
+        _capi.lib().bh_scene_destroy(handle)
+
+
+def bh_camera_set(r_obs: float, incl_deg: float, azim_deg: float = 0.0,
+                  fov_deg: float = 60.0) -> _capi.bh_camera:
+    cam = _capi.bh_camera()
+    check(_capi.lib().bh_camera_set(ctypes.byref(cam), r_obs, incl_deg, azim_deg, fov_deg),
+          "bh_camera_set")
+    return cam
+
+
+def render_opts(mode="mixed", stream=None, **kw) -> _capi.bh_render_opts:
+    """bh_render_opts from keyword arguments (unset fields: tuned defaults)."""
+    o = _capi.bh_render_opts()
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.stream = _stream_ptr(stream)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown render option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream or None
+        except Exception:
+            return None
+        return None
+    return int(getattr(stream, "cuda_stream", stream)) or None
+
+
+def _cams_array(cams):
+    arr = (_capi.bh_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = c
+    return arr
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr() or None
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    return int(t)
+
+
+def bh_render(scene: int, cams, w, h, out_dirs, out_flags, out_rgba8, opts) -> None:
+    """Asynchronous render into device tensors (see include/bh.h)."""
+    n = len(cams)
+    W = (ctypes.c_int * n)(*[int(x) for x in w])
+    H = (ctypes.c_int * n)(*[int(x) for x in h])
+    check(_capi.lib().bh_render(scene, _cams_array(cams), n, W, H, _ptr(out_dirs),
+                                _ptr(out_flags), _ptr(out_rgba8), ctypes.byref(opts)),
+          "bh_render")
+
+
+def bh_render_host(scene: int, cams, w, h, host_dirs, host_flags, host_rgba8, opts) -> None:
+    """Render into host buffers (numpy arrays or CPU tensors); synchronous."""
+    n = len(cams)
+    W = (ctypes.c_int * n)(*[int(x) for x in w])
+    H = (ctypes.c_int * n)(*[int(x) for x in h])
+    check(_capi.lib().bh_render_host(scene, _cams_array(cams), n, W, H, _ptr(host_dirs),
+                                     _ptr(host_flags), _ptr(host_rgba8), ctypes.byref(opts)),
+          "bh_render_host")
+
+
+def bh_scene_sync(scene: int) -> None:
+    check(_capi.lib().bh_scene_sync(scene), "bh_scene_sync")
+
+
+def bh_render_stats(scene: int) -> dict:
+    st = _capi.bh_stats()
+    check(_capi.lib().bh_render_stats(scene, ctypes.byref(st)), "bh_render_stats")
+    out = {name: int(getattr(st, name)) for name, _ in _capi.bh_stats._fields_[:-2]}
+    out["status"] = int(st.status)
+    out["kernel_ms"] = [float(x) for x in st.kernel_ms]
+    return out
+
+
+class Scene:
+    """Owns a bh_scene handle for a workloads.Scene-like description."""
+
+    def __init__(self, scene):
+        self.spec = scene
+        self.handle = bh_scene_create(scene_desc(scene))
+
+    def close(self):
+        if self.handle:
+            bh_scene_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cameras(self, cams):
+        return [bh_camera_set(c.r_obs, c.incl_deg, c.azim_deg, c.fov_deg) for c in cams]
+
+    def render(self, cams, mode="mixed", dirs=None, flags=None, rgba=None, stream=None, **kw):
+        """Render workloads.Camera-like cameras into (new or given) CUDA tensors."""
+        import torch
+        n = sum(int(c.w) * int(c.h) for c in cams)
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        dt = torch.float64 if m == BH_MODE_FP64 else torch.float32
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dirs is None:
+            dirs = torch.empty(2 * n, dtype=dt, device=dev)
+        if flags is None:
+            flags = torch.empty(n, dtype=torch.int16, device=dev)
+        if rgba is None:
+            rgba = torch.empty(n, dtype=torch.int32, device=dev)
+        opts = render_opts(m, stream, **kw)
+        bh_render(self.handle, self.cameras(cams), [c.w for c in cams], [c.h for c in cams],
+                  dirs, flags, rgba, opts)
+        return {"theta": dirs[:n], "phi": dirs[n:], "flags": flags, "rgba": rgba}
+
+    def stats(self) -> dict:
+        return bh_render_stats(self.handle)
+
+
+def render_workload(w, mode=None, **kw) -> dict:
+    """Render a workloads.Workload with its own mode and tolerances."""
+    sc = Scene(w.scene)
+    out = sc.render(w.cameras, mode or w.mode, rtol=w.rtol, atol=w.atol, band=w.band, **kw)
+    out["stats"] = sc.stats()
+    sc.close()
+    return out

@@ -1,0 +1,426 @@
+// C-ABI and host runtime: scenes, cameras, device workspace, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bh.h"
+#include "render.h"
+#include "runtime.h"
+
+using namespace bhk;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+int bh_fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int bh_cuda_fail(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? BH_E_NOMEM : BH_E_CUDA;
+  return bh_fail(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" int bh_version(void) { return BH_ABI_VERSION; }
+
+extern "C" const char* bh_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Device selection guard: run on the scene's device, restore the caller's.
+// ---------------------------------------------------------------------------
+DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+  dev_ = dev;
+}
+DeviceGuard::~DeviceGuard() {
+  if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+// ---------------------------------------------------------------------------
+// Scene
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t grow(T** ptr, size_t* cap, size_t need) {
+  if (*cap >= need && *ptr) return cudaSuccess;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  size_t n = std::max(need, (size_t)1);
+  cudaError_t e = cudaMalloc((void**)ptr, n * sizeof(T));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+extern "C" int bh_scene_create(const bh_scene_desc* desc, bh_scene** out) {
+  if (!desc || !out) return bh_fail(BH_E_INVALID, "bh_scene_create: null argument");
+  *out = nullptr;
+  const double M = desc->mass;
+  if (!(M >= 0.0) || !std::isfinite(M)) return bh_fail(BH_E_INVALID, "mass must be >= 0");
+  if (desc->disk_enabled &&
+      !(desc->disk_r_in > 2.0 * M && desc->disk_r_out > desc->disk_r_in &&
+        std::isfinite(desc->disk_r_out)))
+    return bh_fail(BH_E_INVALID, "disk needs 2M < r_in < r_out");
+  if (desc->n_spheres < 0 || desc->n_spheres > BH_MAX_SPHERES)
+    return bh_fail(BH_E_INVALID, "n_spheres must be in [0, %d]", BH_MAX_SPHERES);
+  if (desc->ic != BH_IC_STATIC && desc->ic != BH_IC_EUCLIDEAN)
+    return bh_fail(BH_E_INVALID, "ic must be BH_IC_STATIC or BH_IC_EUCLIDEAN");
+  double r_min_obj = INFINITY;
+  if (desc->disk_enabled) r_min_obj = desc->disk_r_in;
+  for (int k = 0; k < desc->n_spheres; ++k) {
+    const bh_sphere& s = desc->spheres[k];
+    const double c = std::sqrt(s.center[0] * s.center[0] + s.center[1] * s.center[1] +
+                               s.center[2] * s.center[2]);
+    if (!(s.radius > 0.0) || !(c - s.radius > 2.0 * M) || !std::isfinite(c))
+      return bh_fail(BH_E_INVALID, "sphere %d must have radius > 0 and lie outside r = 2M", k);
+    for (int j = 0; j < 3; ++j)
+      if (!(s.albedo[j] >= 0.0 && s.albedo[j] <= 1.0))
+        return bh_fail(BH_E_INVALID, "sphere %d albedo must be in [0, 1]", k);
+    r_min_obj = std::min(r_min_obj, c - s.radius);
+  }
+  bh_scene* sc = new (std::nothrow) bh_scene();
+  if (!sc) return bh_fail(BH_E_NOMEM, "bh_scene_create: host allocation failed");
+  sc->desc = *desc;
+  SceneK& k = sc->sk;
+  memset(&k, 0, sizeof k);
+  k.M = M;
+  k.M3 = 3.0 * M;
+  // Inside r = 3M an ingoing ray never turns back; with every object
+  // outside 3M the capture decision can be taken there.
+  k.u_capt = (M > 0.0) ? (r_min_obj > 3.0 * M ? 1.0 / (3.0 * M) : 1.0 / (2.0 * M)) : INFINITY;
+  k.b_crit = 3.0 * std::sqrt(3.0) * M;
+  k.disk_on = desc->disk_enabled ? 1 : 0;
+  k.r_in = desc->disk_r_in;
+  k.r_out = desc->disk_r_out;
+  k.n_sph = desc->n_spheres;
+  for (int i = 0; i < desc->n_spheres; ++i) {
+    const bh_sphere& s = desc->spheres[i];
+    double c2 = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      k.c[i][j] = s.center[j];
+      c2 += s.center[j] * s.center[j];
+      k.alb[i][j] = (float)s.albedo[j];
+    }
+    k.c2[i] = c2;
+    k.R[i] = s.radius;
+    k.K[i] = c2 - s.radius * s.radius;
+  }
+  k.seed = desc->sky_seed;
+  k.ic = desc->ic;
+  cudaError_t e = cudaGetDevice(&sc->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, sc->device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sc->d_ws, sizeof(WorkK));
+  if (e == cudaSuccess) e = cudaMemset(sc->d_ws, 0, sizeof(WorkK));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->ev[i]);
+  if (e != cudaSuccess) {
+    const int rc = bh_cuda_fail(e, "bh_scene_create");
+    bh_scene_destroy(sc);
+    return rc;
+  }
+  *out = sc;
+  return BH_OK;
+}
+
+extern "C" void bh_scene_destroy(bh_scene* sc) {
+  if (!sc) return;
+  {
+    DeviceGuard g(sc->device);
+    cudaDeviceSynchronize();
+    cudaFree(sc->d_ws);
+    cudaFree(sc->d_cams);
+    cudaFree(sc->d_spill);
+    cudaFree(sc->d_band);
+    cudaFree(sc->d_stage_dirs);
+    cudaFree(sc->d_stage_flags);
+    cudaFree(sc->d_stage_rgba);
+    for (int i = 0; i < 4; ++i)
+      if (sc->ev[i]) cudaEventDestroy(sc->ev[i]);
+    surrogate_release(sc);
+  }
+  delete sc;
+}
+
+extern "C" int bh_camera_set(bh_camera* cam, double r_obs, double incl_deg, double azim_deg,
+                             double fov_deg) {
+  if (!cam) return bh_fail(BH_E_INVALID, "bh_camera_set: null camera");
+  if (!(r_obs > 0.0) || !std::isfinite(r_obs) || !std::isfinite(incl_deg) ||
+      !std::isfinite(azim_deg) || !(fov_deg > 0.0 && fov_deg < 180.0))
+    return bh_fail(BH_E_INVALID, "bh_camera_set: need r_obs > 0 and 0 < fov < 180");
+  const double pi = 3.14159265358979323846;
+  const double i = incl_deg * pi / 180.0, a = azim_deg * pi / 180.0;
+  cam->r_obs = r_obs;
+  cam->incl_deg = incl_deg;
+  cam->azim_deg = azim_deg;
+  cam->fov_deg = fov_deg;
+  cam->pos[0] = r_obs * std::sin(i) * std::cos(a);
+  cam->pos[1] = r_obs * std::sin(i) * std::sin(a);
+  cam->pos[2] = r_obs * std::cos(i);
+  for (int k = 0; k < 3; ++k) cam->fwd[k] = -cam->pos[k] / r_obs;
+  const double* f = cam->fwd;
+  double upw[3] = {0.0, 0.0, 1.0};
+  double rt[3] = {f[1] * upw[2] - f[2] * upw[1], f[2] * upw[0] - f[0] * upw[2],
+                  f[0] * upw[1] - f[1] * upw[0]};
+  double nr = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+  if (nr < 1e-12) {  // looking along z: world +x is "up"
+    upw[0] = 1.0;
+    upw[2] = 0.0;
+    rt[0] = f[1] * upw[2] - f[2] * upw[1];
+    rt[1] = f[2] * upw[0] - f[0] * upw[2];
+    rt[2] = f[0] * upw[1] - f[1] * upw[0];
+    nr = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+  }
+  for (int k = 0; k < 3; ++k) cam->right[k] = rt[k] / nr;
+  const double* r = cam->right;
+  cam->up[0] = r[1] * f[2] - r[2] * f[1];
+  cam->up[1] = r[2] * f[0] - r[0] * f[2];
+  cam->up[2] = r[0] * f[1] - r[1] * f[0];
+  cam->tan_half = std::tan(0.5 * fov_deg * pi / 180.0);
+  return BH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Render
+// ---------------------------------------------------------------------------
+int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
+                      const int* h, const bh_render_opts* opts) {
+  if (!sc || !cams || !w || !h || !opts) return bh_fail(BH_E_INVALID, "bh_render: null argument");
+  if (n_cams < 1 || n_cams > kMaxCameras)
+    return bh_fail(BH_E_INVALID, "bh_render: n_cams must be in [1, %d]", kMaxCameras);
+  if (opts->mode < BH_MODE_FP64 || opts->mode > BH_MODE_SURROGATE)
+    return bh_fail(BH_E_INVALID, "bh_render: unknown mode %d", opts->mode);
+  for (int i = 0; i < n_cams; ++i) {
+    if (w[i] < 1 || h[i] < 1 || w[i] > 65536 || h[i] > 65536)
+      return bh_fail(BH_E_INVALID, "bh_render: camera %d size %dx%d out of range", i, w[i], h[i]);
+    if (!(cams[i].r_obs > 2.0 * sc->sk.M) || !(cams[i].tan_half > 0.0) ||
+        !std::isfinite(cams[i].tan_half))
+      return bh_fail(BH_E_INVALID, "bh_render: camera %d not set (bh_camera_set) or inside r = 2M", i);
+  }
+  const int tw = opts->tile_w, th = opts->tile_h;
+  if ((tw || th) && (tw < 1 || th < 1 || tw * th != 32))
+    return bh_fail(BH_E_INVALID, "bh_render: tile_w * tile_h must be 32");
+  if (opts->block_size && opts->block_size != 128 && opts->block_size != 256 &&
+      opts->block_size != 512)
+    return bh_fail(BH_E_INVALID, "bh_render: block_size must be 128, 256 or 512");
+  if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->phi_max < 0 || opts->h_max < 0 ||
+      opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0)
+    return bh_fail(BH_E_INVALID, "bh_render: negative option");
+  return BH_OK;
+}
+
+int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                  int tw, int th, long long* n_queue, long long* n_rays) {
+  sc->h_cams.resize(n_cams);
+  long long q = 0, o = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    CamK& c = sc->h_cams[i];
+    const bh_camera& b = cams[i];
+    for (int k = 0; k < 3; ++k) {
+      c.pos[k] = b.pos[k];
+      c.fwd[k] = b.fwd[k];
+      c.right[k] = b.right[k];
+      c.up[k] = b.up[k];
+    }
+    c.sx = b.tan_half;
+    c.sy = b.tan_half * (double)h[i] / (double)w[i];
+    c.r_obs = b.r_obs;
+    c.w = w[i];
+    c.h = h[i];
+    c.tiles_x = (w[i] + tw - 1) / tw;
+    c.tiles_y = (h[i] + th - 1) / th;
+    c.q_off = q;
+    c.out_off = o;
+    q += 32LL * c.tiles_x * c.tiles_y;
+    o += (long long)w[i] * h[i];
+  }
+  if (q >= 0x7FFFFFFFLL || o >= 0x7FFFFFFFLL)
+    return bh_fail(BH_E_INVALID, "bh_render: total ray count must stay below 2^31 - 1");
+  *n_queue = q;
+  *n_rays = o;
+  return BH_OK;
+}
+
+RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
+  RenderConfig c;
+  c.mode = o->mode;
+  const bool f64 = (o->mode == BH_MODE_FP64);
+  c.rtol = o->rtol > 0 ? o->rtol : (f64 ? 1e-10 : 1e-5);
+  c.atol = o->atol > 0 ? o->atol : (f64 ? 1e-10 : 1e-7);
+  c.band = o->band > 0 ? o->band : 0.05;
+  c.phi_max = o->phi_max > 0 ? o->phi_max : 64.0;
+  c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
+  c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
+  const TunedShape t = tuned_shape(sc, o->mode);
+  c.block = o->block_size ? o->block_size : t.block;
+  c.blocks_per_sm = o->blocks_per_sm ? o->blocks_per_sm : t.blocks_per_sm;
+  c.tile_w = o->tile_w ? o->tile_w : t.tile_w;
+  c.tile_h = o->tile_h ? o->tile_h : t.tile_h;
+  c.budget = o->budget ? o->budget : t.budget;
+  c.peri_reset = o->periastron_reset >= 0 ? 1 : 0;
+  c.abort_after = o->abort_after;
+  return c;
+}
+
+int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                  void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts) {
+  const RenderConfig cfg = resolve_config(sc, opts);
+  if (cfg.mode == BH_MODE_SURROGATE) return surrogate_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, cfg);
+  long long n_queue = 0, n_rays = 0;
+  int rc = build_cameras(sc, cams, n_cams, w, h, cfg.tile_w, cfg.tile_h, &n_queue, &n_rays);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)opts->stream;
+  cudaError_t e = grow(&sc->d_cams, &sc->cams_cap, (size_t)n_cams);
+  if (e == cudaSuccess) e = grow(&sc->d_band, &sc->band_cap, (size_t)n_queue);
+  const size_t spill_bytes = (cfg.mode == BH_MODE_FP64 ? sizeof(Spill<double>) : sizeof(Spill<float>));
+  if (e == cudaSuccess) e = grow(&sc->d_spill, &sc->spill_cap, (size_t)n_queue * spill_bytes);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: workspace allocation");
+  e = cudaMemcpyAsync(sc->d_cams, sc->h_cams.data(), n_cams * sizeof(CamK), cudaMemcpyHostToDevice,
+                      stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: upload");
+  Params p;
+  fill_params(sc, cfg, n_cams, n_queue, n_rays, dirs, flags, rgba, &p);
+  LaunchShape ls{sc->num_sms, cfg.block, cfg.blocks_per_sm};
+  const int kmode = cfg.mode == BH_MODE_FP64 ? MODE_FP64 : cfg.mode == BH_MODE_FP32 ? MODE_FP32 : MODE_MIXED;
+  e = launch_render(p, kmode, ls, stream, sc->ev);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: launch");
+  sc->last_stream = stream;
+  sc->timed = true;
+  return BH_OK;
+}
+
+void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long long n_queue,
+                 long long n_rays, void* dirs, uint16_t* flags, uint32_t* rgba, Params* out) {
+  Params& p = *out;
+  memset(&p, 0, sizeof p);
+  p.s = sc->sk;
+  p.cams = sc->d_cams;
+  p.n_cams = n_cams;
+  p.tile_w = cfg.tile_w;
+  p.tile_h = cfg.tile_h;
+  p.budget = cfg.budget;
+  p.n_queue = n_queue;
+  p.n_rays = n_rays;
+  p.rtol = cfg.rtol;
+  p.atol = cfg.atol;
+  p.rtol64 = 1e-10;
+  p.atol64 = 1e-10;
+  p.band = cfg.band;
+  p.phi_max = cfg.phi_max;
+  p.h_max = cfg.h_max;
+  p.max_steps = cfg.max_steps;
+  p.peri_reset = cfg.peri_reset;
+  p.abort_after = cfg.abort_after;
+  p.dirs = dirs;
+  p.flags = flags;
+  p.rgba = rgba;
+  p.ws = sc->d_ws;
+  p.spill = sc->d_spill;
+  p.band_list = sc->d_band;
+}
+
+extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cams, const int* w,
+                         const int* h, void* out_dirs, uint16_t* out_flags, uint32_t* out_rgba8,
+                         const bh_render_opts* opts) {
+  int rc = check_render_args(scene, cams, n_cams, w, h, opts);
+  if (rc) return rc;
+  bh_scene* sc = const_cast<bh_scene*>(scene);
+  DeviceGuard g(sc->device);
+  return render_device(sc, cams, n_cams, w, h, out_dirs, out_flags, out_rgba8, opts);
+}
+
+extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int n_cams,
+                              const int* w, const int* h, void* host_dirs, uint16_t* host_flags,
+                              uint32_t* host_rgba8, const bh_render_opts* opts) {
+  int rc = check_render_args(scene, cams, n_cams, w, h, opts);
+  if (rc) return rc;
+  bh_scene* sc = const_cast<bh_scene*>(scene);
+  DeviceGuard g(sc->device);
+  long long n = 0;
+  for (int i = 0; i < n_cams; ++i) n += (long long)w[i] * h[i];
+  if (n >= 0x7FFFFFFFLL) return bh_fail(BH_E_INVALID, "bh_render_host: too many rays");
+  const size_t dsz = opts->mode == BH_MODE_FP64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = grow((char**)&sc->d_stage_dirs, &sc->stage_dirs_cap, (size_t)(2 * n) * dsz);
+  if (e == cudaSuccess) e = grow(&sc->d_stage_flags, &sc->stage_flags_cap, (size_t)n);
+  if (e == cudaSuccess) e = grow(&sc->d_stage_rgba, &sc->stage_rgba_cap, (size_t)n);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_host: staging allocation");
+  rc = render_device(sc, cams, n_cams, w, h, host_dirs ? sc->d_stage_dirs : nullptr,
+                     host_flags ? sc->d_stage_flags : nullptr, host_rgba8 ? sc->d_stage_rgba : nullptr,
+                     opts);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)opts->stream;
+  if (host_dirs)
+    e = cudaMemcpyAsync(host_dirs, sc->d_stage_dirs, (size_t)(2 * n) * dsz, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess && host_flags)
+    e = cudaMemcpyAsync(host_flags, sc->d_stage_flags, (size_t)n * 2, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess && host_rgba8)
+    e = cudaMemcpyAsync(host_rgba8, sc->d_stage_rgba, (size_t)n * 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_host: copy back");
+  return BH_OK;
+}
+
+extern "C" int bh_scene_sync(const bh_scene* scene) {
+  if (!scene) return bh_fail(BH_E_INVALID, "bh_scene_sync: null scene");
+  DeviceGuard g(scene->device);
+  cudaError_t e = cudaStreamSynchronize(scene->last_stream);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_scene_sync");
+  unsigned status = 0;
+  e = cudaMemcpy(&status, &scene->d_ws->status, sizeof status, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_scene_sync: status");
+  if (status & (BH_STATUS_ABORTED | BH_STATUS_WATCHDOG))
+    return bh_fail(BH_E_DEVICE, "device status 0x%x (%s%s)", status,
+                   (status & BH_STATUS_ABORTED) ? "aborted " : "",
+                   (status & BH_STATUS_WATCHDOG) ? "watchdog" : "");
+  return BH_OK;
+}
+
+extern "C" int bh_render_stats(const bh_scene* scene, bh_stats* out) {
+  if (!scene || !out) return bh_fail(BH_E_INVALID, "bh_render_stats: null argument");
+  DeviceGuard g(scene->device);
+  cudaError_t e = cudaStreamSynchronize(scene->last_stream);
+  WorkK w;
+  if (e == cudaSuccess) e = cudaMemcpy(&w, scene->d_ws, sizeof w, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_stats");
+  memset(out, 0, sizeof *out);
+  out->rays = w.stats[ST_RAYS];
+  out->steps = w.stats[ST_STEPS];
+  out->rejected = w.stats[ST_REJ];
+  out->n_esc = w.stats[ST_ESC];
+  out->n_capt = w.stats[ST_CAPT];
+  out->n_disk = w.stats[ST_DISK];
+  out->n_sphere = w.stats[ST_SPH];
+  out->n_step_limit = w.stats[ST_LIM];
+  out->n_band = w.stats[ST_BAND];
+  out->n_long = w.stats[ST_LONG];
+  out->n_surrogate = w.stats[ST_SURR];
+  out->n_fallback = w.stats[ST_FALLBACK];
+  out->queue_grabs = w.stats[ST_GRABS];
+  out->periastron = w.stats[ST_PERI];
+  out->events = w.stats[ST_EVENTS];
+  out->steps_fp64 = w.stats[ST_STEPS64];
+  out->status = w.status;
+  if (scene->timed) {
+    for (int i = 0; i < 3; ++i) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, scene->ev[i], scene->ev[i + 1]) == cudaSuccess)
+        out->kernel_ms[i] = ms;
+    }
+    float tot = 0.0f;
+    if (cudaEventElapsedTime(&tot, scene->ev[0], scene->ev[3]) == cudaSuccess) out->kernel_ms[3] = tot;
+  }
+  return BH_OK;
+}

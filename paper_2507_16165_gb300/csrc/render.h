@@ -1,0 +1,22 @@
+// Host-side launch interface of the render kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bh_types.cuh"
+
+namespace bhk {
+
+struct LaunchShape {
+  int num_sms;        // streaming multiprocessors of the device
+  int block;          // threads per block
+  int blocks_per_sm;  // 0: the occupancy limit of each kernel
+};
+
+// Launch the kernels of one render (coherent pass, long-ray pass and, in
+// MIXED mode, the FP64 band pass) on `stream`.  ev[0..3], when non-null,
+// are recorded before the first kernel and after each pass.
+cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
+                          cudaEvent_t* ev);
+
+}  // namespace bhk

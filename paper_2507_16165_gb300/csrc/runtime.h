@@ -1,0 +1,84 @@
+// Host runtime internals shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "bh.h"
+#include "bh_types.cuh"
+
+constexpr int kMaxCameras = 4096;
+
+struct SurrogateState;  // trained MLP weights and calibration (surrogate.cu)
+
+// Opaque scene of the C-ABI.
+struct bh_scene {
+  bh_scene_desc desc;
+  bhk::SceneK sk;
+  int device = 0;
+  int num_sms = 1;
+  bhk::WorkK* d_ws = nullptr;
+  bhk::CamK* d_cams = nullptr;
+  size_t cams_cap = 0;
+  std::vector<bhk::CamK> h_cams;
+  char* d_spill = nullptr;  // bytes
+  size_t spill_cap = 0;
+  int* d_band = nullptr;
+  size_t band_cap = 0;
+  void* d_stage_dirs = nullptr;  // bh_render_host staging
+  size_t stage_dirs_cap = 0;
+  uint16_t* d_stage_flags = nullptr;
+  size_t stage_flags_cap = 0;
+  uint32_t* d_stage_rgba = nullptr;
+  size_t stage_rgba_cap = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool timed = false;
+  SurrogateState* surr = nullptr;
+};
+
+// Resolved options of one render.
+struct RenderConfig {
+  int mode;
+  double rtol, atol, band, phi_max, h_max;
+  int max_steps;
+  int block, blocks_per_sm, tile_w, tile_h, budget;
+  int peri_reset;
+  unsigned long long abort_after;
+};
+
+// Launch shape picked by the autotuner (or the built-in default).
+struct TunedShape {
+  int block, blocks_per_sm, tile_w, tile_h, budget;
+};
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+int bh_fail(int code, const char* fmt, ...);
+int bh_cuda_fail(cudaError_t e, const char* what);
+int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
+                      const int* h, const bh_render_opts* opts);
+int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                  int tw, int th, long long* n_queue, long long* n_rays);
+RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o);
+void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long long n_queue,
+                 long long n_rays, void* dirs, uint16_t* flags, uint32_t* rgba, bhk::Params* out);
+int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                  void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts);
+
+// autotune.cu
+TunedShape tuned_shape(const bh_scene* sc, int mode);
+
+// surrogate.cu
+int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                     void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
+                     const RenderConfig& cfg);
+void surrogate_release(bh_scene* sc);

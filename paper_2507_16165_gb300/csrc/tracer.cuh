@@ -1,0 +1,612 @@
+// Device-side ray tracer for the Schwarzschild renderer (sm_103a).
+//
+// One thread owns one ray.  The ray is reduced to its orbital plane through
+// the hole (basis e1 toward the observer, e2 completing the plane), the
+// photon-orbit equation u'' = 3Mu^2 - u (Eq. 1 of Naddell & Ponce, PEARC '25,
+// with the sign fixed by the first integral) is integrated in the azimuth
+// with Dormand-Prince 5(4), events are located on the quintic Hermite
+// interpolant of each accepted step, and the result is mapped back to 3-D and
+// shaded.  Everything is templated on the arithmetic type R (float or double).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bh_types.cuh"
+
+namespace bhk {
+
+// ---------------------------------------------------------------------------
+// Precision-overloaded math.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double m_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_acos(float x) { return acosf(x); }
+__device__ __forceinline__ double m_acos(double x) { return acos(x); }
+__device__ __forceinline__ float m_asin(float x) { return asinf(x); }
+__device__ __forceinline__ double m_asin(double x) { return asin(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
+__device__ __forceinline__ double m_ceil(double x) { return ceil(x); }
+__device__ __forceinline__ float m_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double m_rcp(double x) { return 1.0 / x; }
+
+template <typename R> struct Num;
+template <> struct Num<float> {
+  static constexpr float pi = 3.14159265358979323846f;
+  static constexpr float two_pi = 6.28318530717958647692f;
+  static constexpr float tie = 1e-6f;          // event tie window (rad)
+  static constexpr float radial = 1e-6f;       // |P x d| / |P| below: radial
+  static constexpr int root_iters = 24;        // root iterations (bisection-safe)
+  static constexpr int golden_iters = 32;
+  
+};
+template <> struct Num<double> {
+  static constexpr double pi = 3.14159265358979323846;
+  static constexpr double two_pi = 6.28318530717958647692;
+  static constexpr double tie = 1e-12;
+  static constexpr double radial = 1e-12;
+  static constexpr int root_iters = 60;
+  static constexpr int golden_iters = 70;
+};
+
+// ---------------------------------------------------------------------------
+// Dormand-Prince 5(4) (Dormand & Prince 1980) in the stage form used here:
+// stage s has U_s = u + h sum_j a_sj V_j, V_s = v + h sum_j a_sj F_j with
+// V_1 = v, F_1 = accel(u) and F_s = accel(U_s); the 7th stage is the
+// fifth-order solution (first same as last).  E_j are the differences
+// between the fifth- and fourth-order weights.
+// ---------------------------------------------------------------------------
+#define DP_A21 (1.0 / 5.0)
+#define DP_A31 (3.0 / 40.0)
+#define DP_A32 (9.0 / 40.0)
+#define DP_A41 (44.0 / 45.0)
+#define DP_A42 (-56.0 / 15.0)
+#define DP_A43 (32.0 / 9.0)
+#define DP_A51 (19372.0 / 6561.0)
+#define DP_A52 (-25360.0 / 2187.0)
+#define DP_A53 (64448.0 / 6561.0)
+#define DP_A54 (-212.0 / 729.0)
+#define DP_A61 (9017.0 / 3168.0)
+#define DP_A62 (-355.0 / 33.0)
+#define DP_A63 (46732.0 / 5247.0)
+#define DP_A64 (49.0 / 176.0)
+#define DP_A65 (-5103.0 / 18656.0)
+#define DP_B1 (35.0 / 384.0)
+#define DP_B3 (500.0 / 1113.0)
+#define DP_B4 (125.0 / 192.0)
+#define DP_B5 (-2187.0 / 6784.0)
+#define DP_B6 (11.0 / 84.0)
+#define DP_E1 (71.0 / 57600.0)
+#define DP_E3 (-71.0 / 16695.0)
+#define DP_E4 (71.0 / 1920.0)
+#define DP_E5 (-17253.0 / 339200.0)
+#define DP_E6 (22.0 / 525.0)
+#define DP_E7 (-1.0 / 40.0)
+
+template <typename R>
+__device__ __forceinline__ R accel(R M3, R u) {
+  return u * m_fma(M3, u, R(-1));  // 3Mu^2 - u
+}
+
+// One attempted step.  Returns the fifth-order state (un, vn), the FSAL
+// derivative fn = accel(un), and the squared Hairer error norm
+// err2 = ((eu/su)^2 + (ev/sv)^2) / 2 with su = atol + rtol max(|u|, |un|).
+template <typename R>
+__device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R atol,
+                                            R& un, R& vn, R& fn, R& err2) {
+  R U, V;
+  // stage 2
+  U = m_fma(h, R(DP_A21) * v, u);
+  V = m_fma(h, R(DP_A21) * f1, v);
+  const R V2 = V, F2 = accel(M3, U);
+  // stage 3
+  U = m_fma(h, m_fma(R(DP_A32), V2, R(DP_A31) * v), u);
+  V = m_fma(h, m_fma(R(DP_A32), F2, R(DP_A31) * f1), v);
+  const R V3 = V, F3 = accel(M3, U);
+  // stage 4
+  U = m_fma(h, m_fma(R(DP_A43), V3, m_fma(R(DP_A42), V2, R(DP_A41) * v)), u);
+  V = m_fma(h, m_fma(R(DP_A43), F3, m_fma(R(DP_A42), F2, R(DP_A41) * f1)), v);
+  const R V4 = V, F4 = accel(M3, U);
+  // stage 5
+  U = m_fma(h, m_fma(R(DP_A54), V4, m_fma(R(DP_A53), V3, m_fma(R(DP_A52), V2, R(DP_A51) * v))), u);
+  V = m_fma(h, m_fma(R(DP_A54), F4, m_fma(R(DP_A53), F3, m_fma(R(DP_A52), F2, R(DP_A51) * f1))), v);
+  const R V5 = V, F5 = accel(M3, U);
+  // stage 6
+  U = m_fma(h, m_fma(R(DP_A65), V5, m_fma(R(DP_A64), V4, m_fma(R(DP_A63), V3,
+                m_fma(R(DP_A62), V2, R(DP_A61) * v)))), u);
+  V = m_fma(h, m_fma(R(DP_A65), F5, m_fma(R(DP_A64), F4, m_fma(R(DP_A63), F3,
+                m_fma(R(DP_A62), F2, R(DP_A61) * f1)))), v);
+  const R V6 = V, F6 = accel(M3, U);
+  // stage 7 = fifth-order solution
+  un = m_fma(h, m_fma(R(DP_B6), V6, m_fma(R(DP_B5), V5, m_fma(R(DP_B4), V4,
+                m_fma(R(DP_B3), V3, R(DP_B1) * v)))), u);
+  vn = m_fma(h, m_fma(R(DP_B6), F6, m_fma(R(DP_B5), F5, m_fma(R(DP_B4), F4,
+                m_fma(R(DP_B3), F3, R(DP_B1) * f1)))), v);
+  fn = accel(M3, un);
+  // embedded error (fifth minus fourth order)
+  const R eu = h * m_fma(R(DP_E7), vn, m_fma(R(DP_E6), V6, m_fma(R(DP_E5), V5,
+                m_fma(R(DP_E4), V4, m_fma(R(DP_E3), V3, R(DP_E1) * v)))));
+  const R ev = h * m_fma(R(DP_E7), fn, m_fma(R(DP_E6), F6, m_fma(R(DP_E5), F5,
+                m_fma(R(DP_E4), F4, m_fma(R(DP_E3), F3, R(DP_E1) * f1)))));
+  const R su = m_fma(rtol, m_max(m_abs(u), m_abs(un)), atol);
+  const R sv = m_fma(rtol, m_max(m_abs(v), m_abs(vn)), atol);
+  const R ru = eu * m_rcp(su), rv = ev * m_rcp(sv);
+  err2 = R(0.5) * m_fma(ru, ru, rv * rv);
+}
+
+// Step-size factor 0.9 err^(-1/5) clamped to [0.2, 10], from err2 = err^2.
+// Computed in single precision for both arithmetic types: it only steers the
+// step size (a relative change of 1e-7 in h moves the solution by far less
+// than the tolerance); acceptance uses err2 <= 1 in the working precision.
+template <typename R>
+__device__ __forceinline__ R step_factor(R err2) {
+  const float e2 = (float)err2;
+  float fac;
+  if (!(e2 > 0.0f)) {
+    fac = (e2 == 0.0f) ? 10.0f : 0.2f;  // zero error grows, NaN shrinks
+  } else {
+    fac = 0.9f * exp2f(-0.1f * __log2f(e2));
+    fac = fminf(10.0f, fmaxf(0.2f, fac));
+  }
+  return R(fac);
+}
+
+// Starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), capped at
+// cap rad.
+template <typename R>
+__device__ R initial_step(R M3, R u, R v, R rtol, R atol, R cap) {
+  const R scu = m_fma(rtol, m_abs(u), atol), scv = m_fma(rtol, m_abs(v), atol);
+  const R fu = v, fv = accel(M3, u);
+  const R iu = R(1) / scu, iv = R(1) / scv;
+  const R d0 = m_sqrt(R(0.5) * ((u * iu) * (u * iu) + (v * iv) * (v * iv)));
+  const R d1 = m_sqrt(R(0.5) * ((fu * iu) * (fu * iu) + (fv * iv) * (fv * iv)));
+  const R h0 = (d0 < R(1e-5) || d1 < R(1e-5)) ? R(1e-6) : R(0.01) * d0 / d1;
+  const R u1 = m_fma(h0, fu, u), v1 = m_fma(h0, fv, v);
+  const R gu = v1 - fu, gv = accel(M3, u1) - fv;
+  const R d2 = m_sqrt(R(0.5) * ((gu * iu) * (gu * iu) + (gv * iv) * (gv * iv))) / h0;
+  const R dm = m_max(d1, d2);
+  R h1;
+  if (dm <= R(1e-15)) {
+    h1 = m_max(R(1e-6), h0 * R(1e-3));
+  } else {
+    h1 = R(exp2f(0.2f * __log2f((float)(R(0.01) / dm))));
+  }
+  return m_min(m_min(R(100) * h0, h1), cap);
+}
+
+// ---------------------------------------------------------------------------
+// Quintic Hermite interpolant of u on [pa, pa + h] from u, h u', h^2 u''.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Hermite {
+  R pa, h, ih;
+  R u0, d0, s0, u1, d1, s1;
+  __device__ __forceinline__ void make(R pa_, R h_, R ua, R va, R fa, R ub, R vb, R fb) {
+    pa = pa_;
+    h = h_;
+    ih = R(1) / h_;
+    u0 = ua;
+    d0 = h_ * va;
+    s0 = h_ * h_ * fa;
+    u1 = ub;
+    d1 = h_ * vb;
+    s1 = h_ * h_ * fb;
+  }
+  // value at normalised t in [0, 1]
+  __device__ __forceinline__ R val_t(R t) const {
+    const R t2 = t * t, t3 = t2 * t;
+    // basis in Horner form in t for the t^3.. terms
+    const R h0 = R(1) + t3 * m_fma(t, m_fma(R(-6), t, R(15)), R(-10));
+    const R h1 = t + t3 * m_fma(t, m_fma(R(-3), t, R(8)), R(-6));
+    const R h2 = R(0.5) * t2 * (R(1) + t * m_fma(t, m_fma(R(-1), t, R(3)), R(-3)));
+    const R h3 = t3 * m_fma(t, m_fma(R(6), t, R(-15)), R(10));
+    const R h4 = t3 * m_fma(t, m_fma(R(-3), t, R(7)), R(-4));
+    const R h5 = R(0.5) * t3 * m_fma(t, t - R(2), R(1));
+    return u0 * h0 + d0 * h1 + s0 * h2 + u1 * h3 + d1 * h4 + s1 * h5;
+  }
+  // d/dt of the interpolant
+  __device__ __forceinline__ R dval_t(R t) const {
+    const R t2 = t * t;
+    const R g0 = t2 * m_fma(t, m_fma(R(-30), t, R(60)), R(-30));
+    const R g1 = R(1) + t2 * m_fma(t, m_fma(R(-15), t, R(32)), R(-18));
+    const R g2 = R(0.5) * t * (R(2) + t * m_fma(t, m_fma(R(-5), t, R(12)), R(-9)));
+    const R g3 = t2 * m_fma(t, m_fma(R(30), t, R(-60)), R(30));
+    const R g4 = t2 * m_fma(t, m_fma(R(-15), t, R(28)), R(-12));
+    const R g5 = R(0.5) * t2 * m_fma(t, m_fma(R(5), t, R(-8)), R(3));
+    return u0 * g0 + d0 * g1 + s0 * g2 + u1 * g3 + d1 * g4 + s1 * g5;
+  }
+  __device__ __forceinline__ R t_of(R phi) const { return (phi - pa) * ih; }
+  __device__ __forceinline__ R u_at(R phi) const { return val_t(t_of(phi)); }
+  __device__ __forceinline__ R v_at(R phi) const { return dval_t(t_of(phi)) * ih; }
+};
+
+// Root t in [lo, hi] of val_t(t) - target, given a sign change, by Newton
+// steps kept inside a shrinking bracket (bisection when Newton leaves it).
+template <typename R>
+__device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
+  R flo = H.val_t(lo) - target;
+  R t = lo + (hi - lo) * (flo / (flo - (H.val_t(hi) - target)));
+  if (!(t > lo && t < hi)) t = R(0.5) * (lo + hi);
+  for (int it = 0; it < Num<R>::root_iters; ++it) {
+    const R f = H.val_t(t) - target;
+    if (f == R(0)) return t;
+    if ((f > R(0)) == (flo > R(0))) {
+      lo = t;
+      flo = f;
+    } else {
+      hi = t;
+    }
+    const R df = H.dval_t(t);
+    R tn = t - f / df;
+    if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
+    if (m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7)) {
+      t = tn;
+      break;
+    }
+    t = tn;
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Per-ray state.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Ray {
+  R u, v, f, phi, h;     // state, FSAL derivative, azimuth, next step
+  R e1x, e1y, e1z, e2x, e2y, e2z;  // plane basis
+  R phi_node;            // next disk node angle (> phi), or +inf
+  R phi_sph;             // next sphere-window start, or +inf
+  R u0, v0;              // initial state (for the periastron reset)
+  unsigned sph_mask;     // spheres whose in-plane circle is non-empty
+  int steps;             // attempted steps
+  int out;               // output pixel index
+  unsigned aux;          // BAND / FP64 provenance bits, periastron-done bit
+};
+
+constexpr unsigned kAuxPeriDone = 1u << 16;
+
+// Event produced when a ray terminates.
+template <typename R>
+struct Hit {
+  unsigned flags;  // low byte BH_FLAG_*, high byte sphere id
+  R phi;           // event angle
+  R u, v;          // state at the event
+};
+
+// Camera ray through pixel (px, py) (pixel centres, row 0 at the top).
+template <typename R>
+__device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3], R d[3]) {
+  const R sx = (R(2) * (R(px) + R(0.5)) / R(c.w) - R(1)) * R(c.sx);
+  const R sy = (R(1) - R(2) * (R(py) + R(0.5)) / R(c.h)) * R(c.sy);
+  R dd[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    P[k] = R(c.pos[k]);
+    dd[k] = R(c.fwd[k]) + sx * R(c.right[k]) + sy * R(c.up[k]);
+  }
+  const R inv = R(1) / m_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = dd[k] * inv;
+}
+
+// Angular window [ws, we] of sphere k in the ray's plane: the directions
+// from the hole that meet the sphere's in-plane circle, the first one whose
+// end lies at or after phi_from.  Evaluated in single precision for both
+// arithmetic types (it only gates the exact test) and widened by 1e-4 rad.
+template <typename R>
+__device__ __forceinline__ float sphere_window(const SceneK& s, const Ray<R>& r, int k,
+                                               float phi_from, float* we) {
+  const float c0 = (float)s.c[k][0], c1 = (float)s.c[k][1], c2 = (float)s.c[k][2];
+  const float cx = c0 * (float)r.e1x + c1 * (float)r.e1y + c2 * (float)r.e1z;
+  const float cy = c0 * (float)r.e2x + c1 * (float)r.e2y + c2 * (float)r.e2z;
+  const float rho2 = cx * cx + cy * cy;
+  const float rp2 = fmaxf(0.0f, (float)(s.R[k] * s.R[k]) - ((float)s.c2[k] - rho2));
+  float pc = atan2f(cy, cx);
+  if (pc < 0.0f) pc += 6.28318530717958647692f;
+  const float dp = asinf(fminf(1.0f, sqrtf(rp2 / rho2))) + 1e-4f;
+  const float m = ceilf((phi_from - pc - dp) * 0.15915494309189535f);
+  const float ws = pc - dp + 6.28318530717958647692f * m;
+  *we = pc + dp + 6.28318530717958647692f * m;
+  return ws;
+}
+
+template <typename R>
+__device__ __forceinline__ R next_sphere_window(const SceneK& s, const Ray<R>& r, R phi_from) {
+  float best = INFINITY;
+  unsigned m = r.sph_mask;
+  while (m) {
+    const int k = __ffs(m) - 1;
+    m &= m - 1;
+    float we;
+    best = fminf(best, sphere_window(s, r, k, (float)phi_from, &we));
+  }
+  return R(best);
+}
+
+// Orbital-plane set-up of a camera ray.  Returns 0 for a ray to integrate,
+// 1 for a radial ray (handled by the caller with straight-line geometry).
+template <typename R>
+__device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, Ray<R>& r,
+                           R* b_out, R* cos_a_out) {
+  const R ir = R(1) / r_obs;
+  r.e1x = P[0] * ir;
+  r.e1y = P[1] * ir;
+  r.e1z = P[2] * ir;
+  R cr0 = P[1] * d[2] - P[2] * d[1];
+  R cr1 = P[2] * d[0] - P[0] * d[2];
+  R cr2 = P[0] * d[1] - P[1] * d[0];
+  const R sn = m_sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+  const R cos_a = d[0] * r.e1x + d[1] * r.e1y + d[2] * r.e1z;
+  *cos_a_out = cos_a;
+  if (sn < Num<R>::radial * r_obs) {
+    *b_out = R(0);
+    return 1;
+  }
+  const R isn = R(1) / sn;
+  const R nx = cr0 * isn, ny = cr1 * isn, nz = cr2 * isn;
+  r.e2x = ny * r.e1z - nz * r.e1y;
+  r.e2y = nz * r.e1x - nx * r.e1z;
+  r.e2z = nx * r.e1y - ny * r.e1x;
+  const R sin_a = d[0] * r.e2x + d[1] * r.e2y + d[2] * r.e2z;
+  const R M = R(s.M);
+  const R u0 = ir;
+  const R cot = cos_a / sin_a;
+  R b;
+  if (s.ic == 0) {
+    b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * ir);
+    r.v0 = -u0 * cot * m_sqrt(R(1) - R(2) * M * u0);
+  } else {
+    b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * sin_a * sin_a * ir);
+    r.v0 = -u0 * cot;
+  }
+  *b_out = b;
+  r.u0 = u0;
+  r.u = u0;
+  r.v = r.v0;
+  r.f = accel(R(s.M3), u0);
+  r.phi = R(0);
+  // disk nodes: z(phi) ~ cos(phi) e1z + sin(phi) e2z
+  r.phi_node = R(INFINITY);
+  if (s.disk_on) {
+    const R a = r.e1z, c = r.e2z;
+    if (a * a + c * c >= R(sizeof(R) == 8 ? 1e-24 : 1e-12)) {
+      R p0 = m_atan2(-a, c);
+      if (p0 < R(0)) p0 += Num<R>::pi;
+      if (p0 >= Num<R>::pi) p0 -= Num<R>::pi;
+      r.phi_node = (p0 > R(0)) ? p0 : Num<R>::pi;
+    }
+  }
+  // spheres cut by the plane
+  unsigned mask = 0;
+  for (int k = 0; k < s.n_sph; ++k) {
+    const R sd = nx * R(s.c[k][0]) + ny * R(s.c[k][1]) + nz * R(s.c[k][2]);
+    if (m_abs(sd) < R(s.R[k])) mask |= 1u << k;
+  }
+  r.sph_mask = mask;
+  r.phi_sph = mask ? next_sphere_window(s, r, R(0)) : R(INFINITY);
+  return 0;
+}
+
+// g(phi) < 0 inside sphere k's in-plane circle (u^2 (|p - c'|^2 - R'^2)).
+template <typename R>
+__device__ __forceinline__ R sphere_g(R cx, R cy, R K, R phi, R u) {
+  R sp, cp;
+  m_sincos(phi, &sp, &cp);
+  return m_fma(K * u, u, m_fma(R(-2) * u, m_fma(cx, cp, cy * sp), R(1)));
+}
+
+// First entry into sphere k during the accepted step [pa, pb] (u at the
+// ends ua, ub from the interpolant H).  A step's arc never leaves the
+// straight chord between its end points by more than 3M q^2 h^2 / 8 in
+// radius (the deviation w from the chord obeys w'' + w = 3Mu^2 with zero end
+// values; q = u_max / u_min on the step), so steps whose chord passes farther
+// than R' + that margin from the circle are rejected without a search.
+template <typename R>
+__device__ bool sphere_entry(const SceneK& s, const Ray<R>& r, int k, const Hermite<R>& H,
+                             R pa, R pb, R* phi_hit) {
+  float wef;
+  const float wsf = sphere_window(s, r, k, (float)pa, &wef);
+  if (R(wsf) > pb || R(wef) < pa) return false;
+  R lo = m_max(pa, R(wsf)), hi = m_min(pb, R(wef));
+  if (!(hi > lo)) return false;
+  const R c0 = R(s.c[k][0]), c1 = R(s.c[k][1]), c2 = R(s.c[k][2]);
+  const R cx = c0 * r.e1x + c1 * r.e1y + c2 * r.e1z;
+  const R cy = c0 * r.e2x + c1 * r.e2y + c2 * r.e2z;
+  const R K = R(s.K[k]);
+  const R rp2 = R(s.R[k]) * R(s.R[k]) - (R(s.c2[k]) - (cx * cx + cy * cy));
+  if (!(rp2 > R(0))) return false;
+  const R ulo = H.u_at(lo), uhi = H.u_at(hi);
+  if (ulo > R(0) && uhi > R(0)) {
+    R sa, ca, sb, cb;
+    m_sincos(lo, &sa, &ca);
+    m_sincos(hi, &sb, &cb);
+    const R ia = R(1) / ulo, ib = R(1) / uhi;
+    const R ax = ca * ia, ay = sa * ia;
+    const R bx = cb * ib - ax, by = sb * ib - ay;
+    const R qx = cx - ax, qy = cy - ay;
+    const R bb = m_fma(bx, bx, by * by);
+    R t = bb > R(0) ? m_fma(qx, bx, qy * by) / bb : R(0);
+    t = m_min(R(1), m_max(R(0), t));
+    const R dx = qx - t * bx, dy = qy - t * by;
+    const R q = m_max(ulo, uhi) / m_min(ulo, uhi);
+    const R hh = hi - lo;
+    const R margin = R(0.47) * R(s.M3) * q * q * hh * hh + R(1e-6);
+    const R reach = m_sqrt(rp2) + margin;
+    if (m_fma(dx, dx, dy * dy) > reach * reach) return false;
+  }
+  // careful search on the interpolant
+  const R glo = sphere_g(cx, cy, K, lo, ulo);
+  if (!(glo > R(0))) {
+    *phi_hit = lo;
+    return true;
+  }
+  R a_lo = lo, a_hi;
+  const R ghi = sphere_g(cx, cy, K, hi, uhi);
+  if (ghi <= R(0)) {
+    a_hi = hi;
+  } else {
+    // golden-section search for the minimum of g on [lo, hi]
+    R x0 = lo, x3 = hi;
+    const R gr = R(0.6180339887498949);
+    R x1 = x3 - gr * (x3 - x0), x2 = x0 + gr * (x3 - x0);
+    R g1 = sphere_g(cx, cy, K, x1, H.u_at(x1));
+    R g2 = sphere_g(cx, cy, K, x2, H.u_at(x2));
+    bool found = false;
+    for (int it = 0; it < Num<R>::golden_iters; ++it) {
+      if (g1 <= R(0) || g2 <= R(0)) {
+        found = true;
+        break;
+      }
+      if (g1 < g2) {
+        x3 = x2;
+        x2 = x1;
+        g2 = g1;
+        x1 = x3 - gr * (x3 - x0);
+        g1 = sphere_g(cx, cy, K, x1, H.u_at(x1));
+      } else {
+        x0 = x1;
+        x1 = x2;
+        g1 = g2;
+        x2 = x0 + gr * (x3 - x0);
+        g2 = sphere_g(cx, cy, K, x2, H.u_at(x2));
+      }
+      if (x3 - x0 < R(sizeof(R) == 8 ? 1e-13 : 1e-6)) break;
+    }
+    if (!found) return false;
+    a_hi = (g1 <= R(0)) ? x1 : x2;
+    a_lo = x0;
+  }
+  // bisection on the entry: g(a_lo) > 0 >= g(a_hi)
+  for (int it = 0; it < Num<R>::root_iters; ++it) {
+    const R mid = R(0.5) * (a_lo + a_hi);
+    if (!(mid > a_lo && mid < a_hi)) break;
+    if (sphere_g(cx, cy, K, mid, H.u_at(mid)) > R(0))
+      a_lo = mid;
+    else
+      a_hi = mid;
+    if (a_hi - a_lo < R(sizeof(R) == 8 ? 1e-14 : 1e-7)) break;
+  }
+  *phi_hit = a_hi;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Shading and stores.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned quant8(float c) {
+  float q = floorf(fmaf(255.0f, c, 0.5f));
+  q = fminf(255.0f, fmaxf(0.0f, q));
+  return (unsigned)q;
+}
+
+__device__ __forceinline__ unsigned pack_rgba(float r, float g, float b) {
+  return quant8(r) | (quant8(g) << 8) | (quant8(b) << 16) | (255u << 24);
+}
+
+template <typename R>
+__device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R phi) {
+  int i = (int)m_floor(R(16) * theta / Num<R>::pi);
+  int j = (int)m_floor(R(32) * phi / Num<R>::two_pi);
+  i = min(15, max(0, i));
+  j = min(31, max(0, j));
+  const bool light = ((i + j) & 1) == 0;
+  const unsigned long long hsh = splitmix64(seed * 2654435761ull + (unsigned long long)(32 * i + j));
+  float rgb[3];
+  const float base[3] = {light ? 0.9f : 0.1f, light ? 0.9f : 0.1f, light ? 0.9f : 0.25f};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float slice = (float)((hsh >> (16 * c)) & 0xFFFFFFull);
+    // (0.75 + 0.25 slice / 2^24), evaluated in double-free single precision
+    rgb[c] = base[c] * (0.75f + 0.25f * (slice * (1.0f / 16777216.0f)));
+  }
+  return pack_rgba(rgb[0], rgb[1], rgb[2]);
+}
+
+template <typename R>
+__device__ __forceinline__ void dir_angles(R x, R y, R z, R* th, R* ph) {
+  z = m_min(R(1), m_max(R(-1), z));
+  *th = m_acos(z);
+  R p = m_atan2(y, x);
+  if (p < R(0)) p += Num<R>::two_pi;
+  *ph = p;
+}
+
+// Store one finished ray.  OutR is the element type of out_dirs.
+template <typename OutR>
+__device__ __forceinline__ void store_ray(const Params& p, int out, OutR th, OutR ph, unsigned flags,
+                                          unsigned rgba) {
+  if (p.dirs) {
+    OutR* d = reinterpret_cast<OutR*>(p.dirs);
+    d[out] = th;
+    d[(long long)p.n_rays + out] = ph;
+  }
+  if (p.flags) p.flags[out] = (uint16_t)flags;
+  if (p.rgba) p.rgba[out] = rgba;
+}
+
+// Map a terminated ray back to 3-D, shade it and store it.
+template <typename R, typename OutR>
+__device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) {
+  const SceneK& s = p.s;
+  const unsigned fl = hit.flags & 0xFFu;
+  const unsigned flags = hit.flags | (r.aux & 0xFFu);
+  if (fl == BH_FLAG_CAPT || fl == BH_FLAG_STEP_LIMIT) {
+    store_ray<OutR>(p, r.out, OutR(NAN), OutR(NAN), flags, 255u << 24);
+    return;
+  }
+  R sp, cp;
+  m_sincos(hit.phi, &sp, &cp);
+  const R dx = cp * r.e1x + sp * r.e2x;
+  const R dy = cp * r.e1y + sp * r.e2y;
+  const R dz = cp * r.e1z + sp * r.e2z;
+  R th, ph;
+  dir_angles(dx, dy, dz, &th, &ph);
+  unsigned rgba;
+  if (fl == BH_FLAG_ESC) {
+    rgba = sky_rgba<R>(s.seed, th, ph);
+  } else if (fl == BH_FLAG_DISK) {
+    const float rr = (float)(R(1) / hit.u);
+    const float t = exp2f(0.75f * __log2f((float)s.r_in / rr));
+    const float k = fmaf(0.7f, t, 0.3f);
+    rgba = pack_rgba(k, fmaf(0.65f, t, 0.35f) * k, fmaf(0.9f * t, t, 0.1f) * k);
+  } else {  // sphere
+    const int id = (int)(hit.flags >> 8);
+    const R u = hit.u, v = hit.v;
+    const R iu = R(1) / u;
+    // tangent d x/d phi scaled by u^2
+    R T[3] = {u * (-sp * r.e1x + cp * r.e2x) - v * dx, u * (-sp * r.e1y + cp * r.e2y) - v * dy,
+              u * (-sp * r.e1z + cp * r.e2z) - v * dz};
+    const R it = R(1) / m_sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+    const R iR = R(1) / R(s.R[id]);
+    const R N0 = (dx * iu - R(s.c[id][0])) * iR, N1 = (dy * iu - R(s.c[id][1])) * iR,
+            N2 = (dz * iu - R(s.c[id][2])) * iR;
+    const float ndt = (float)(-(N0 * T[0] + N1 * T[1] + N2 * T[2]) * it);
+    const float lam = 0.25f + 0.75f * fmaxf(0.0f, ndt);
+    rgba = pack_rgba(s.alb[id][0] * lam, s.alb[id][1] * lam, s.alb[id][2] * lam);
+  }
+  store_ray<OutR>(p, r.out, OutR(th), OutR(ph), flags, rgba);
+}
+
+}  // namespace bhk

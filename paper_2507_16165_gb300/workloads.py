@@ -128,18 +128,18 @@ def config1(size: int = 64) -> Workload:
 
 def config2(size: int = 1024, mode: str = "fp64") -> Workload:
     """1024^2, r_obs = 40M, inclination 80 deg, disk [6M, 20M], sky seed 0."""
-    tol = 1e-10 if mode == "fp64" else 1e-6
+    rtol, atol = (1e-10, 1e-10) if mode == "fp64" else (1e-5, 1e-7)
     return Workload(f"c2_{mode}_{size}", Scene(mass=1.0, disk=(6.0, 20.0), sky_seed=0),
-                    (Camera(40.0, 80.0, size, size),), mode, tol, tol)
+                    (Camera(40.0, 80.0, size, size),), mode, rtol, atol)
 
 
 def config3(size: int = 4096, mode: str = "mixed") -> Workload:
     """4096^2, r_obs = 50M, inclination 75 deg, disk [6M, 30M], 8 spheres
     (seed 0), FP32 stepping with FP64 in the band |b - 3 sqrt(3) M| < 0.05M."""
-    tol = 1e-10 if mode == "fp64" else 1e-6
+    rtol, atol = (1e-10, 1e-10) if mode == "fp64" else (1e-5, 1e-7)
     sc = Scene(mass=1.0, disk=(6.0, 30.0), spheres=seeded_spheres(0), sky_seed=0)
     return Workload(f"c3_{mode}_{size}", sc, (Camera(50.0, 75.0, size, size),), mode,
-                    tol, tol, band=0.05)
+                    rtol, atol, band=0.05)
 
 
 def config4(size: int = 4096, spheres: bool = True) -> Workload:
@@ -157,7 +157,7 @@ def config5(n_cams: int = 64, scale: int = 1) -> Workload:
     if scale > 1:
         cams = tuple(replace(c, w=max(8, c.w // scale), h=max(8, c.h // scale)) for c in cams)
     return Workload(f"c5_batch{n_cams}", Scene(mass=1.0, disk=(6.0, 20.0), sky_seed=0),
-                    cams, "fp32", 1e-6, 1e-6)
+                    cams, "fp32", 1e-5, 1e-7)
 
 
 def surrogate_samples(n: int, seed: int = 0, b_lo: float = 3.0 * math.sqrt(3.0) + 1e-4,

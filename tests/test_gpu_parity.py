@@ -1,0 +1,124 @@
+"""GPU renders through the C-ABI against the CPU oracle, element by element.
+
+Bars: flags bit-exact outside the oracle's ambiguity mask; exit directions
+within 1e-9 rad (FP64) or 1e-4 rad (FP32, MIXED) at the 99.9th percentile;
+at most 0.1% of RGBA8 pixels off by more than 1.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+from gpu_util import render
+from paper_2507_16165_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _tol(mode):
+    return (1e-10, 1e-10) if mode == "fp64" else (1e-5, 1e-7)
+
+
+def _check(w, mode, nthreads=8, **kw):
+    rtol, atol = _tol(mode)
+    got, st = render(w.scene, w.cameras, mode, rtol=rtol, atol=atol, band=w.band, **kw)
+    ref = oracle.render(w.scene, w.cameras, parity.oracle_opts(mode), nthreads=nthreads)
+    m = parity.compare(got, ref, mode)
+    parity.assert_parity(m, mode)
+    assert st["status"] == 0
+    assert st["rays"] == w.n_rays, st
+    return m, st
+
+
+def _ragged(w, wd, ht):
+    return replace(w, cameras=tuple(replace(c, w=wd, h=ht) for c in w.cameras))
+
+
+CASES = {
+    "c1_fp64_64": (W.config1(64), "fp64"),
+    "c2_fp64_ragged_70x45": (_ragged(W.config2(64, "fp64"), 70, 45), "fp64"),
+    "c3_fp64_96": (W.config3(96, "fp64"), "fp64"),
+    "c2_fp32_256": (W.config2(256, "fp32"), "fp32"),
+    "c2_mixed_256": (W.config2(256, "mixed"), "mixed"),
+    "c3_fp32_ragged_250x190": (_ragged(W.config3(64, "fp32"), 250, 190), "fp32"),
+    "c3_mixed_256": (W.config3(256, "mixed"), "mixed"),
+    "c5_batch6_fp32": (W.config5(6, scale=16), "fp32"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_parity(name):
+    w, mode = CASES[name]
+    _check(w, mode)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_tiny_and_degenerate_images(mode):
+    """1x1, single-row, single-column and odd sizes (the centre pixel of an
+    odd image is an exactly radial ray)."""
+    base = W.config3(8, mode)
+    for wd, ht in [(1, 1), (1, 7), (7, 1), (9, 9), (33, 17)]:
+        _check(_ragged(base, wd, ht), mode, nthreads=2)
+
+
+def test_pole_camera_and_zero_mass():
+    """Camera on the +z axis (inclination 0: the 'up' fallback) and M = 0
+    (straight lines) in FP64."""
+    sc = W.Scene(mass=1.0, disk=(6.0, 20.0), sky_seed=3)
+    _check(W.Workload("pole", sc, (W.Camera(25.0, 0.0, 40, 40),), "fp64", 1e-10, 1e-10), "fp64")
+    flat = W.Scene(mass=0.0, disk=(4.0, 12.0), spheres=W.seeded_spheres(1, 3), sky_seed=1)
+    _check(W.Workload("flat", flat, (W.Camera(30.0, 60.0, 48, 32, azim_deg=10.0),), "fp64",
+                      1e-10, 1e-10), "fp64")
+
+
+def test_euclidean_initial_conditions():
+    """The paper's 'linear direction' reading of the initial conditions."""
+    sc = replace(W.config2(64, "fp64").scene, ic=1)
+    _check(W.Workload("eucl", sc, (W.Camera(40.0, 80.0, 64, 64),), "fp64", 1e-10, 1e-10), "fp64")
+
+
+def test_multi_camera_ordering_fp64():
+    """Outputs are camera-major, row-major: a batch equals the concatenation
+    of single-camera renders."""
+    w = W.config5(3, scale=32)
+    got, _ = render(w.scene, w.cameras, "fp64", rtol=1e-10, atol=1e-10)
+    off = 0
+    for c in w.cameras:
+        one, _ = render(w.scene, [c], "fp64", rtol=1e-10, atol=1e-10)
+        n = c.w * c.h
+        assert np.array_equal(one["flags"], got["flags"][off:off + n])
+        assert np.array_equal(one["rgba"], got["rgba"][off:off + n])
+        off += n
+
+
+def test_abort_after_reports_device_status():
+    """Host-injected abort word: the render stops early and the scene reports
+    BH_E_DEVICE with the ABORTED status bit (no device trap)."""
+    import torch
+
+    import paper_2507_16165_gb300 as bh
+    w = W.config2(256, "fp32")
+    sc = bh.Scene(w.scene)
+    try:
+        sc.render(w.cameras, "fp32", abort_after=64)
+        torch.cuda.synchronize()
+        with pytest.raises(bh.BHError) as ei:
+            bh.bh_scene_sync(sc.handle)
+        assert ei.value.code == -4
+        assert sc.stats()["status"] & 1
+        # the scene stays usable
+        sc.render(w.cameras, "fp32")
+        bh.bh_scene_sync(sc.handle)
+    finally:
+        sc.close()
+
+
+def test_stats_account_for_every_ray():
+    w = W.config3(128, "mixed")
+    _, st = render(w.scene, w.cameras, "mixed", band=0.05)
+    assert st["rays"] == 128 * 128
+    assert st["n_esc"] + st["n_capt"] + st["n_disk"] + st["n_sphere"] + st["n_step_limit"] == st["rays"]
+    assert st["steps"] >= st["rejected"]
+    assert st["n_band"] > 0 and st["periastron"] > 0
