@@ -208,6 +208,36 @@ int bh_scene_sync(const bh_scene *scene);
 /* Statistics of the scene's last render (synchronises its stream). */
 int bh_render_stats(const bh_scene *scene, bh_stats *out);
 
+/* ---- render without allocating ----------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: hosts that give all device memory to their own
+ * pool or a fixed budget and forbid other allocations, and real-time loops
+ * in which an allocation may synchronise the device or fail in mid-frame.
+ *
+ * It renders like bh_render in BH_MODE_FP32 or BH_MODE_FP64 (other modes:
+ * BH_E_UNSUPPORTED) but allocates nothing and needs no bh_scene: the scene
+ * is read from desc on every call, and the only scratch -- the work-queue
+ * counter, status and statistics words and the camera table -- lives in one
+ * fixed library-owned device array of about 10 KB, present on every device
+ * that loads the library until the process exits.  Every ray is finished by
+ * the coherent pass (no long-ray list), so results equal bh_render's.
+ *   - desc, cams, w, h: host, as for bh_scene_create / bh_render;
+ *     n_cams <= BH_NOALLOC_MAX_CAMERAS, else BH_E_INVALID.
+ *   - out_dirs, out_flags, out_rgba8: caller-owned device buffers laid out
+ *     as for bh_render.
+ *   - Asynchronous on opts->stream; the camera table is copied on it.
+ *   - The first call on a device looks up the scratch array's device
+ *     address (with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (counters are cleared at the start of each call): calls that overlap
+ *     on the GPU, on any streams, race and must be serialised by the caller.
+ * Errors: BH_E_INVALID, BH_E_UNSUPPORTED, BH_E_CUDA. */
+#define BH_NOALLOC_MAX_CAMERAS 64
+int bh_render_noalloc(const bh_scene_desc *desc, const bh_camera *cams, int n_cams,
+                      const int *w, const int *h, void *out_dirs, uint16_t *out_flags,
+                      uint32_t *out_rgba8, const bh_render_opts *opts);
+
 #ifdef __cplusplus
 }
 #endif

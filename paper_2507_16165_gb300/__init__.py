@@ -23,7 +23,7 @@ from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # no
 
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
            "bh_camera_set", "bh_render", "bh_render_host", "bh_scene_sync",
-           "bh_render_stats", "Scene", "render_opts", "render_workload"]
+           "bh_render_stats", "bh_render_noalloc", "Scene", "render_opts", "render_workload"]
 
 
 def bh_version() -> int:
@@ -133,6 +133,18 @@ def bh_render_host(scene: int, cams, w, h, host_dirs, host_flags, host_rgba8, op
     check(_capi.lib().bh_render_host(scene, _cams_array(cams), n, W, H, _ptr(host_dirs),
                                      _ptr(host_flags), _ptr(host_rgba8), ctypes.byref(opts)),
           "bh_render_host")
+
+
+def bh_render_noalloc(desc: _capi.bh_scene_desc, cams, w, h, out_dirs, out_flags, out_rgba8,
+                      opts) -> None:
+    """bh_render_noalloc of the C-ABI: FP32 / FP64 render into caller device
+    buffers using only the library's fixed scratch array (no allocation)."""
+    n = len(cams)
+    W = (ctypes.c_int * n)(*[int(x) for x in w])
+    H = (ctypes.c_int * n)(*[int(x) for x in h])
+    check(_capi.lib().bh_render_noalloc(ctypes.byref(desc), _cams_array(cams), n, W, H,
+                                        _ptr(out_dirs), _ptr(out_flags), _ptr(out_rgba8),
+                                        ctypes.byref(opts)), "bh_render_noalloc")
 
 
 def bh_scene_sync(scene: int) -> None:

@@ -85,7 +85,10 @@ SIGNATURES = [
                             ctypes.POINTER(bh_render_opts)]),
     ("bh_scene_sync", _I, [_P]),
     ("bh_render_stats", _I, [_P, ctypes.POINTER(bh_stats)]),
+    ("bh_render_noalloc", _I, [ctypes.POINTER(bh_scene_desc), ctypes.POINTER(bh_camera), _I,
+                               _P, _P, _P, _P, _P, ctypes.POINTER(bh_render_opts)]),
 ]
+BH_NOALLOC_MAX_CAMERAS = 64
 
 
 def lib(path: str = LIB_PATH) -> ctypes.CDLL:

@@ -480,4 +480,21 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
   return cudaGetLastError();
 }
 
+cudaError_t launch_coherent_only(const Params& p, int mode, const LaunchShape& ls,
+                                 cudaStream_t stream) {
+  const int block = ls.block;
+  if (mode == MODE_FP64) {
+    auto k = k_coherent<double, MODE_FP64, double>;
+    const int per_sm = ls.blocks_per_sm > 0 ? ls.blocks_per_sm : occupancy(k, block);
+    k<<<ls.num_sms * per_sm, block, 0, stream>>>(p);
+  } else if (mode == MODE_FP32) {
+    auto k = k_coherent<float, MODE_FP32, float>;
+    const int per_sm = ls.blocks_per_sm > 0 ? ls.blocks_per_sm : occupancy(k, block);
+    k<<<ls.num_sms * per_sm, block, 0, stream>>>(p);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace bhk

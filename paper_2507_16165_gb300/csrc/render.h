@@ -19,4 +19,10 @@ struct LaunchShape {
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
                           cudaEvent_t* ev);
 
+// Launch only the coherent pass (mode MODE_FP32 or MODE_FP64).  With
+// p.budget >= p.max_steps no ray is moved to the long-ray list, so the pass
+// finishes every ray itself and needs no spill or band storage.
+cudaError_t launch_coherent_only(const Params& p, int mode, const LaunchShape& ls,
+                                 cudaStream_t stream);
+
 }  // namespace bhk
