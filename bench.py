@@ -43,7 +43,9 @@ FLOP_PER_STEP = 2 * 59 + 26 + 4
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9}
-KERNELS_PER_RENDER = {"mixed": 3, "fp32": 2, "fp64": 2}
+# kernels one render launches: coherent + long-ray passes, and in MIXED the
+# band pre-pass and the FP64 band pass
+KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2}
 
 
 def workload(form: str, size: int):
@@ -99,7 +101,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -370,7 +372,7 @@ def run_ours(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("mixed", "fp32", "fp64"), default="mixed")

@@ -123,13 +123,14 @@ typedef struct bh_render_opts {
   double rtol, atol;  /* Dormand-Prince tolerances (0: 1e-10 / 1e-10 in FP64,
                          1e-5 / 1e-7 in FP32 and MIXED)                     */
   double band;        /* FP64 / fallback band half-width in b (0: 0.05 M)    */
+  double band_rtol;   /* rtol = atol of the MIXED FP64 band pass (0: 1e-9)   */
   double phi_max;     /* azimuth cap in rad (0: 64)                          */
   int max_steps;      /* attempted-step cap per ray (0: 100000)              */
   double h_max;       /* largest step in rad (0: none in FP64, 0.3 otherwise;
                          the quintic event interpolant needs short steps)   */
   void *stream;       /* cudaStream_t                                       */
   /* launch shape; 0 selects the tuned value for this device and mode      */
-  int block_size;     /* threads per block: 128, 256 or 512                 */
+  int block_size;     /* threads per block: 64, 128 or 256                  */
   int blocks_per_sm;  /* resident blocks per SM in the persistent grid      */
   int tile_w, tile_h; /* pixel tile that one warp takes (tile_w*tile_h = 32)*/
   int budget;         /* steps a ray may take in the coherent pass before it
@@ -154,7 +155,10 @@ typedef struct bh_stats {
   uint64_t events;        /* event-handling passes (nodes, windows, roots)   */
   uint64_t steps_fp64;    /* attempted steps taken in FP64 (part of steps)   */
   uint32_t status;        /* BH_STATUS_* bits of the last render             */
-  float kernel_ms[4];     /* device time of the render's kernels (0 if not timed)*/
+  float kernel_ms[4];     /* device time of the last render: [0] coherent pass
+                             (with the MIXED band pre-pass), [1] long-ray pass,
+                             [2] FP64 band pass (MIXED; it overlaps [0] and [1]
+                             on a side stream), [3] whole render            */
 } bh_stats;
 
 /* Library version (BH_ABI_VERSION). */

@@ -49,7 +49,8 @@ class bh_camera(ctypes.Structure):
 
 class bh_render_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
-                ("band", ctypes.c_double), ("phi_max", ctypes.c_double),
+                ("band", ctypes.c_double), ("band_rtol", ctypes.c_double),
+                ("phi_max", ctypes.c_double),
                 ("max_steps", ctypes.c_int), ("h_max", ctypes.c_double),
                 ("stream", ctypes.c_void_p),
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),

@@ -9,5 +9,9 @@ TunedShape tuned_shape(const bh_scene* sc, int mode) {
   t.tile_w = 8;
   t.tile_h = 4;
   t.budget = (mode == BH_MODE_FP64) ? 256 : 48;
+  // MIXED: leave room on every SM for the band pass that runs alongside
+  if (mode == BH_MODE_MIXED) t.blocks_per_sm = 3;
+  t.band_lanes = 32;
+  t.band_warps = 4;
   return t;
 }

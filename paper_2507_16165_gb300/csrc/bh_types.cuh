@@ -9,6 +9,27 @@ namespace bhk {
 
 constexpr int kMaxSph = BH_MAX_SPHERES;
 
+// Scene constants in the kernel's arithmetic type (a float copy for the
+// FP32 kernels, so they convert nothing from double on the slow FP64 pipe).
+template <typename R>
+struct SceneR {
+  R M, M3, u_capt, b_crit, r_in, r_out;
+  R c[kMaxSph][3], c2[kMaxSph], rad[kMaxSph], K[kMaxSph];
+};
+
+// Camera constants in the kernel's arithmetic type.
+template <typename R>
+struct CamR {
+  R pos[3], fwd[3], right[3], up[3];
+  R sx, sy, r_obs;
+};
+
+// Tolerances and caps in the kernel's arithmetic type.
+template <typename R>
+struct TolR {
+  R rtol, atol, phi_max, h_max, band;
+};
+
 // Scene constants, passed by value in every kernel's parameter block.
 struct SceneK {
   double M, M3;        // mass and 3M
@@ -25,6 +46,8 @@ struct SceneK {
   float alb[kMaxSph][3];
   unsigned long long seed;
   int ic;
+  SceneR<float> f;
+  SceneR<double> d;
 };
 
 // One camera in device memory.  Its rays occupy queue slots
@@ -36,6 +59,8 @@ struct CamK {
   double r_obs;
   int w, h, tiles_x, tiles_y;
   long long q_off, out_off;
+  CamR<float> f;
+  CamR<double> d;
 };
 
 enum StatId {
@@ -93,6 +118,47 @@ struct Params {
   WorkK* ws;
   void* spill;        // Spill<R>[n_queue]
   int* band_list;     // queue slots deferred to FP64 [n_queue]
+  unsigned* band_bits;  // one bit per queue slot: set when the slot is a band ray
+  int band_lanes;       // lanes of a band-pass warp that take rays (1..32)
+  TolR<float> tf;     // main pass, FP32 kernels
+  TolR<double> td;    // main pass, FP64 mode
+  TolR<double> tb;    // FP64 band pass of the MIXED mode
 };
+
+template <typename R> __host__ __device__ __forceinline__ const SceneR<R>& SR(const SceneK& s);
+template <> __host__ __device__ __forceinline__ const SceneR<float>& SR<float>(const SceneK& s) { return s.f; }
+template <> __host__ __device__ __forceinline__ const SceneR<double>& SR<double>(const SceneK& s) { return s.d; }
+template <typename R> __host__ __device__ __forceinline__ const CamR<R>& CR(const CamK& c);
+template <> __host__ __device__ __forceinline__ const CamR<float>& CR<float>(const CamK& c) { return c.f; }
+template <> __host__ __device__ __forceinline__ const CamR<double>& CR<double>(const CamK& c) { return c.d; }
+
+// Fill the typed copies of the scene, camera and tolerance constants.
+template <typename R>
+inline void fill_scene_r(const SceneK& s, SceneR<R>* o) {
+  o->M = R(s.M);
+  o->M3 = R(s.M3);
+  o->u_capt = R(s.u_capt);
+  o->b_crit = R(s.b_crit);
+  o->r_in = R(s.r_in);
+  o->r_out = R(s.r_out);
+  for (int k = 0; k < kMaxSph; ++k) {
+    for (int j = 0; j < 3; ++j) o->c[k][j] = R(s.c[k][j]);
+    o->c2[k] = R(s.c2[k]);
+    o->rad[k] = R(s.R[k]);
+    o->K[k] = R(s.K[k]);
+  }
+}
+template <typename R>
+inline void fill_cam_r(const CamK& c, CamR<R>* o) {
+  for (int j = 0; j < 3; ++j) {
+    o->pos[j] = R(c.pos[j]);
+    o->fwd[j] = R(c.fwd[j]);
+    o->right[j] = R(c.right[j]);
+    o->up[j] = R(c.up[j]);
+  }
+  o->sx = R(c.sx);
+  o->sy = R(c.sy);
+  o->r_obs = R(c.r_obs);
+}
 
 }  // namespace bhk

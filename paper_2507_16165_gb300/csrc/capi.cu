@@ -121,11 +121,21 @@ extern "C" int bh_scene_create(const bh_scene_desc* desc, bh_scene** out) {
   }
   k.seed = desc->sky_seed;
   k.ic = desc->ic;
+  fill_scene_r(k, &k.f);
+  fill_scene_r(k, &k.d);
   cudaError_t e = cudaGetDevice(&sc->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, sc->device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&sc->d_ws, sizeof(WorkK));
   if (e == cudaSuccess) e = cudaMemset(sc->d_ws, 0, sizeof(WorkK));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->ev[i]);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->band_ev[i]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->join, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    e = cudaStreamCreateWithPriority(&sc->side, cudaStreamNonBlocking, greatest);
+  }
   if (e != cudaSuccess) {
     const int rc = bh_cuda_fail(e, "bh_scene_create");
     bh_scene_destroy(sc);
@@ -149,6 +159,12 @@ extern "C" void bh_scene_destroy(bh_scene* sc) {
     cudaFree(sc->d_stage_rgba);
     for (int i = 0; i < 4; ++i)
       if (sc->ev[i]) cudaEventDestroy(sc->ev[i]);
+    for (int i = 0; i < 2; ++i)
+      if (sc->band_ev[i]) cudaEventDestroy(sc->band_ev[i]);
+    if (sc->fork) cudaEventDestroy(sc->fork);
+    if (sc->join) cudaEventDestroy(sc->join);
+    if (sc->side) cudaStreamDestroy(sc->side);
+    cudaFree(sc->d_bits);
     surrogate_release(sc);
   }
   delete sc;
@@ -212,10 +228,11 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
   const int tw = opts->tile_w, th = opts->tile_h;
   if ((tw || th) && (tw < 1 || th < 1 || tw * th != 32))
     return bh_fail(BH_E_INVALID, "bh_render: tile_w * tile_h must be 32");
-  if (opts->block_size && opts->block_size != 128 && opts->block_size != 256 &&
-      opts->block_size != 512)
-    return bh_fail(BH_E_INVALID, "bh_render: block_size must be 128, 256 or 512");
-  if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->phi_max < 0 || opts->h_max < 0 ||
+  if (opts->block_size && opts->block_size != 64 && opts->block_size != 128 &&
+      opts->block_size != 256)
+    return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
+  if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
+      opts->phi_max < 0 || opts->h_max < 0 ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
   return BH_OK;
@@ -243,6 +260,8 @@ int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
     c.tiles_y = (h[i] + th - 1) / th;
     c.q_off = q;
     c.out_off = o;
+    fill_cam_r(c, &c.f);
+    fill_cam_r(c, &c.d);
     q += 32LL * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }
@@ -260,6 +279,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.rtol = o->rtol > 0 ? o->rtol : (f64 ? 1e-10 : 1e-5);
   c.atol = o->atol > 0 ? o->atol : (f64 ? 1e-10 : 1e-7);
   c.band = o->band > 0 ? o->band : 0.05;
+  c.band_rtol = o->band_rtol > 0 ? o->band_rtol : 1e-9;
   c.phi_max = o->phi_max > 0 ? o->phi_max : 64.0;
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
@@ -269,6 +289,8 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.tile_w = o->tile_w ? o->tile_w : t.tile_w;
   c.tile_h = o->tile_h ? o->tile_h : t.tile_h;
   c.budget = o->budget ? o->budget : t.budget;
+  c.band_lanes = t.band_lanes;
+  c.band_warps = t.band_warps;
   c.peri_reset = o->periastron_reset >= 0 ? 1 : 0;
   c.abort_after = o->abort_after;
   return c;
@@ -286,6 +308,8 @@ int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
   if (e == cudaSuccess) e = grow(&sc->d_band, &sc->band_cap, (size_t)n_queue);
   const size_t spill_bytes = (cfg.mode == BH_MODE_FP64 ? sizeof(Spill<double>) : sizeof(Spill<float>));
   if (e == cudaSuccess) e = grow(&sc->d_spill, &sc->spill_cap, (size_t)n_queue * spill_bytes);
+  if (e == cudaSuccess && cfg.mode == BH_MODE_MIXED)
+    e = grow(&sc->d_bits, &sc->bits_cap, (size_t)(n_queue / 32 + 1));
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: workspace allocation");
   e = cudaMemcpyAsync(sc->d_cams, sc->h_cams.data(), n_cams * sizeof(CamK), cudaMemcpyHostToDevice,
                       stream);
@@ -294,11 +318,20 @@ int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
   Params p;
   fill_params(sc, cfg, n_cams, n_queue, n_rays, dirs, flags, rgba, &p);
   LaunchShape ls{sc->num_sms, cfg.block, cfg.blocks_per_sm};
+  if (cfg.mode == BH_MODE_MIXED) {
+    p.band_bits = sc->d_bits;
+    ls.side = sc->side;
+    ls.fork = sc->fork;
+    ls.join = sc->join;
+    ls.band_ev = sc->band_ev;
+    ls.band_warps = cfg.band_warps;
+  }
   const int kmode = cfg.mode == BH_MODE_FP64 ? MODE_FP64 : cfg.mode == BH_MODE_FP32 ? MODE_FP32 : MODE_MIXED;
   e = launch_render(p, kmode, ls, stream, sc->ev);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: launch");
   sc->last_stream = stream;
   sc->timed = true;
+  sc->band_used = (cfg.mode == BH_MODE_MIXED);
   return BH_OK;
 }
 
@@ -316,8 +349,8 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.n_rays = n_rays;
   p.rtol = cfg.rtol;
   p.atol = cfg.atol;
-  p.rtol64 = 1e-10;
-  p.atol64 = 1e-10;
+  p.rtol64 = cfg.band_rtol;
+  p.atol64 = cfg.band_rtol;
   p.band = cfg.band;
   p.phi_max = cfg.phi_max;
   p.h_max = cfg.h_max;
@@ -330,6 +363,14 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.ws = sc->d_ws;
   p.spill = sc->d_spill;
   p.band_list = sc->d_band;
+  p.band_lanes = cfg.band_lanes;
+  fill_tolerances(p);
+}
+
+void fill_tolerances(Params& p) {
+  p.tf = TolR<float>{(float)p.rtol, (float)p.atol, (float)p.phi_max, (float)p.h_max, (float)p.band};
+  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band};
+  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band};
 }
 
 extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cams, const int* w,
@@ -414,10 +455,17 @@ extern "C" int bh_render_stats(const bh_scene* scene, bh_stats* out) {
   out->steps_fp64 = w.stats[ST_STEPS64];
   out->status = w.status;
   if (scene->timed) {
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 2; ++i) {
       float ms = 0.0f;
       if (cudaEventElapsedTime(&ms, scene->ev[i], scene->ev[i + 1]) == cudaSuccess)
         out->kernel_ms[i] = ms;
+    }
+    float ms = 0.0f;
+    if (scene->band_used) {
+      if (cudaEventElapsedTime(&ms, scene->band_ev[0], scene->band_ev[1]) == cudaSuccess)
+        out->kernel_ms[2] = ms;
+    } else if (cudaEventElapsedTime(&ms, scene->ev[2], scene->ev[3]) == cudaSuccess) {
+      out->kernel_ms[2] = ms;
     }
     float tot = 0.0f;
     if (cudaEventElapsedTime(&tot, scene->ev[0], scene->ev[3]) == cudaSuccess) out->kernel_ms[3] = tot;

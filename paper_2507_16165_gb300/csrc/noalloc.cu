@@ -99,6 +99,8 @@ int noalloc_scene(const bh_scene_desc* d, SceneK* k) {
   k->n_sph = d->n_spheres;
   k->seed = d->sky_seed;
   k->ic = d->ic;
+  fill_scene_r(*k, &k->f);
+  fill_scene_r(*k, &k->d);
   return BH_OK;
 }
 
@@ -117,9 +119,9 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   if ((opts->tile_w || opts->tile_h) &&
       (opts->tile_w < 1 || opts->tile_h < 1 || opts->tile_w * opts->tile_h != 32))
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: tile_w * tile_h must be 32");
-  if (opts->block_size && opts->block_size != 128 && opts->block_size != 256 &&
-      opts->block_size != 512)
-    return bh_fail(BH_E_INVALID, "bh_render_noalloc: block_size must be 128, 256 or 512");
+  if (opts->block_size && opts->block_size != 64 && opts->block_size != 128 &&
+      opts->block_size != 256)
+    return bh_fail(BH_E_INVALID, "bh_render_noalloc: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->phi_max < 0 || opts->h_max < 0 ||
       opts->max_steps < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: negative option");
@@ -152,6 +154,8 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     c.tiles_y = (h[i] + th - 1) / th;
     c.q_off = q;
     c.out_off = o;
+    fill_cam_r(c, &c.f);
+    fill_cam_r(c, &c.d);
     q += 32LL * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }
@@ -200,6 +204,8 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   p.ws = ws;
   p.spill = nullptr;
   p.band_list = nullptr;
+  p.band_lanes = 32;
+  fill_tolerances(p);
   LaunchShape ls{num_sms, opts->block_size ? opts->block_size : 256, opts->blocks_per_sm};
   e = launch_coherent_only(p, f64 ? MODE_FP64 : MODE_FP32, ls, stream);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_noalloc: launch");

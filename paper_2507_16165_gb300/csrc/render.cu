@@ -18,6 +18,17 @@ namespace bhk {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Tolerances of a pass: FP32 kernels, FP64 mode, or the MIXED FP64 band.
+template <typename R, int MODE> struct TolPick;
+template <int MODE> struct TolPick<float, MODE> {
+  static __device__ __forceinline__ const TolR<float>& get(const Params& p) { return p.tf; }
+};
+template <int MODE> struct TolPick<double, MODE> {
+  static __device__ __forceinline__ const TolR<double>& get(const Params& p) {
+    return MODE == MODE_BAND64 ? p.tb : p.td;
+  }
+};
+
 struct LocalStats {
   unsigned c[ST_N];
   __device__ __forceinline__ void zero() {
@@ -72,12 +83,13 @@ template <typename R, typename OutR>
 __device__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a, int out,
                            unsigned aux, LocalStats& st) {
   const SceneK& s = p.s;
+  const SceneR<R>& S = SR<R>(s);
   R best = R(INFINITY);
   int bk = -1;
   for (int k = 0; k < s.n_sph; ++k) {
-    const R o0 = P[0] - R(s.c[k][0]), o1 = P[1] - R(s.c[k][1]), o2 = P[2] - R(s.c[k][2]);
+    const R o0 = P[0] - S.c[k][0], o1 = P[1] - S.c[k][1], o2 = P[2] - S.c[k][2];
     const R bq = o0 * d[0] + o1 * d[1] + o2 * d[2];
-    const R cq = o0 * o0 + o1 * o1 + o2 * o2 - R(s.R[k]) * R(s.R[k]);
+    const R cq = o0 * o0 + o1 * o1 + o2 * o2 - S.rad[k] * S.rad[k];
     const R disc = bq * bq - cq;
     if (disc < R(0)) continue;
     const R t = -bq - m_sqrt(disc);
@@ -88,13 +100,13 @@ __device__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a,
   }
   const R r0 = m_sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
   const bool ingoing = cos_a < R(0);
-  const R t_hole = ingoing ? r0 - R(2) * R(s.M) : R(INFINITY);
+  const R t_hole = ingoing ? r0 - R(2) * S.M : R(INFINITY);
   unsigned flags;
   if (bk >= 0 && best < t_hole) {
     const R x0 = P[0] + best * d[0], x1 = P[1] + best * d[1], x2 = P[2] + best * d[2];
-    const R iR = R(1) / R(s.R[bk]);
-    const R N0 = (x0 - R(s.c[bk][0])) * iR, N1 = (x1 - R(s.c[bk][1])) * iR,
-            N2 = (x2 - R(s.c[bk][2])) * iR;
+    const R iR = R(1) / S.rad[bk];
+    const R N0 = (x0 - S.c[bk][0]) * iR, N1 = (x1 - S.c[bk][1]) * iR,
+            N2 = (x2 - S.c[bk][2]) * iR;
     const float lam = 0.25f + 0.75f * fmaxf(0.0f, (float)(-(N0 * d[0] + N1 * d[1] + N2 * d[2])));
     const R ix = R(1) / m_sqrt(x0 * x0 + x1 * x1 + x2 * x2);
     R th, ph;
@@ -102,7 +114,7 @@ __device__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a,
     flags = BH_FLAG_SPHERE | ((unsigned)bk << 8) | aux;
     store_ray<OutR>(p, out, OutR(th), OutR(ph), flags,
                     pack_rgba(s.alb[bk][0] * lam, s.alb[bk][1] * lam, s.alb[bk][2] * lam));
-  } else if (ingoing && s.M > 0.0) {
+  } else if (ingoing && S.M > R(0)) {
     flags = BH_FLAG_CAPT | aux;
     store_ray<OutR>(p, out, OutR(NAN), OutR(NAN), flags, 255u << 24);
   } else {
@@ -114,11 +126,36 @@ __device__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a,
   st.count_flag(flags);
 }
 
+// Periastron of the orbit through the FP32 initial state (u0, v0): the
+// middle root u_p of P(u) = 2M u^3 - u^2 + E0, E0 = v0^2 + u0^2 (1 - 2M u0).
+// FP32 start from the trigonometric form of the cubic's roots,
+//   u_p = cos(acos(1 - 54 M^2 E0) / 3 - 2 pi / 3) / (3M) + 1/(6M),
+// one FP32 Newton step, then one Newton step with P evaluated in FP64 (the
+// slope only scales the step and stays in FP32).  NaN when there is no
+// turning point (b <= 3 sqrt(3) M).  Solved once per ray at set-up, where a
+// warp's lanes run it together.
+__device__ __forceinline__ float periastron64(float M, float u0f, float v0f) {
+  const double u0 = u0f, v0 = v0f, m2 = 2.0 * (double)M;
+  const double E0 = fma(v0, v0, u0 * u0 * fma(-m2, u0, 1.0));
+  const float E = (float)E0;
+  if (!(M > 0.0f)) return sqrtf(E);
+  const float x = fmaf(-54.0f * M * M, E, 1.0f);
+  if (!(x > -1.0f)) return NAN;
+  const float im = 1.0f / M;
+  float u = fmaf(0.33333334f * im, cosf(acosf(x) * 0.33333334f - 2.0943951f), 0.16666667f * im);
+  const float m2f = 2.0f * M;
+  u -= fmaf(u * u, fmaf(m2f, u, -1.0f), E) / (u * fmaf(3.0f * m2f, u, -2.0f));
+  const double ud = u;
+  const double f = fma(ud * ud, fma(m2, ud, -1.0), E0);
+  return (float)(ud - f * (double)(1.0f / (u * fmaf(3.0f * m2f, u, -2.0f))));
+}
+
 // Set up the ray of queue slot q.  Returns true when the ray is to be
 // integrated by the caller; false when it was padding, finished directly
 // (radial) or deferred to the FP64 band list.
 template <typename R, int MODE, typename OutR>
 __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out) {
+  if (MODE == MODE_MIXED && p.band_bits && ((p.band_bits[q >> 5] >> (q & 31)) & 1u)) return false;
   int cam, px, py, out;
   if (!slot_pixel(p, q, &cam, &px, &py, &out)) return false;
   const CamK& c = p.cams[cam];
@@ -128,25 +165,70 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   r.aux = (MODE == MODE_FP64 || MODE == MODE_BAND64) ? BH_FLAG_FP64 : 0u;
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
-  if (plane_setup<R>(p.s, P, d, R(c.r_obs), r, &b, &cos_a)) {
+  if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, r, &b, &cos_a)) {
     radial_ray<R, OutR>(p, P, d, cos_a, out, r.aux, st);
     return false;
   }
   *b_out = b;
-  if (MODE == MODE_MIXED) {
-    if (m_abs(b - R(p.s.b_crit)) < R(p.band)) {
+  const TolR<R>& tol = TolPick<R, MODE>::get(p);
+  if (MODE == MODE_MIXED && !p.band_bits) {
+    if (m_abs(b - SR<R>(p.s).b_crit) < tol.band) {
       const unsigned long long k = atomicAdd(&p.ws->band_count, 1ull);
       p.band_list[k] = (int)q;
       st.c[ST_BAND]++;
       return false;
     }
   }
+  if (MODE == MODE_MIXED) r.up = R(periastron64(p.s.f.M, float(r.u), float(r.v)));
   r.steps = 0;
   const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
-  const R rtol = R(d64 && MODE == MODE_BAND64 ? p.rtol64 : p.rtol);
-  const R atol = R(d64 && MODE == MODE_BAND64 ? p.atol64 : p.atol);
-  r.h = initial_step<R>(R(p.s.M3), r.u, r.v, rtol, atol, R(d64 ? 0.01 : m_min(1.0, p.h_max)));
+  r.h = initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol,
+                        d64 ? R(0.01) : m_min(R(1), tol.h_max));
   return true;
+}
+
+// Band pre-pass of the MIXED mode: one warp per 32-slot tile computes each
+// ray's impact parameter in FP32 and marks |b - 3 sqrt(3) M| < band in the
+// bitmap (one word per tile) and the FP64 band list (one atomic per warp).
+// The coherent pass then skips marked slots, so the two FP64 and FP32
+// passes can run at the same time.
+__global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Params p) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const SceneR<float>& S = p.s.f;
+  const float bc = S.b_crit, band = p.tf.band, M = S.M;
+  LocalStats st;
+  st.zero();
+  for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       t * 32 < p.n_queue; t += warps) {
+    const long long q = t * 32 + lane;
+    int cam, px, py, out;
+    bool in_band = false;
+    if (slot_pixel(p, q, &cam, &px, &py, &out)) {
+      const CamK& c = p.cams[cam];
+      float P[3], d[3];
+      camera_ray<float>(c, px, py, P, d);
+      const float r0 = c.f.r_obs, ir = 1.0f / r0;
+      const float c0 = P[1] * d[2] - P[2] * d[1], c1 = P[2] * d[0] - P[0] * d[2],
+                  c2 = P[0] * d[1] - P[1] * d[0];
+      const float sin_a = sqrtf(c0 * c0 + c1 * c1 + c2 * c2) * ir;
+      const float b = (p.s.ic == 0) ? r0 * sin_a * rsqrtf(1.0f - 2.0f * M * ir)
+                                    : r0 * sin_a * rsqrtf(1.0f - 2.0f * M * sin_a * sin_a * ir);
+      in_band = fabsf(b - bc) < band;
+    }
+    const unsigned bits = __ballot_sync(kFull, in_band);
+    unsigned long long base = 0;
+    if (lane == 0) {
+      p.band_bits[t] = bits;
+      if (bits) base = atomicAdd(&p.ws->band_count, (unsigned long long)__popc(bits));
+    }
+    base = __shfl_sync(kFull, base, 0);
+    if (in_band) {
+      p.band_list[base + __popc(bits & ((1u << lane) - 1u))] = (int)q;
+      st.c[ST_BAND]++;
+    }
+  }
+  st.flush(p.ws);
 }
 
 // Turning point of the FP32 orbit: v changes sign inside [0, 1] of H.
@@ -166,20 +248,6 @@ __device__ __forceinline__ R turning_t(const Hermite<R>& H, R M3) {
   return t;
 }
 
-// Periastron u_p in FP64: Newton on 2M u^3 - u^2 + E0 = 0 with
-// E0 = v0^2 + u0^2 - 2M u0^3 from the FP32 initial state, started at the
-// interpolated u (two steps; the reciprocal slope in single precision).
-__device__ __forceinline__ double periastron64(double M, double u0, double v0, double ug) {
-  const double E0 = v0 * v0 + u0 * u0 - 2.0 * M * u0 * u0 * u0;
-  double u = ug;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double f = fma(2.0 * M * u, u * u, fma(-u, u, E0));
-    const double df = u * fma(6.0 * M, u, -2.0);
-    u -= f * (double)(1.0f / (float)df);
-  }
-  return u;
-}
 
 template <typename R>
 __device__ __forceinline__ void consider(int type, R ph, unsigned id, int& bt, R& bp, unsigned& bid) {
@@ -202,7 +270,8 @@ template <typename R, int MODE>
 __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& pb, R h,
                             bool peri, Hit<R>& hit, LocalStats& st) {
   const SceneK& s = p.s;
-  const R M3 = R(s.M3);
+  const SceneR<R>& S = SR<R>(s);
+  const R M3 = S.M3;
   const R pa = r.phi;
   Hermite<R> H;
   H.make(pa, h, r.u, r.v, r.f, un, vn, fn);
@@ -211,12 +280,10 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
     // state back on the orbit of the initial conditions, (u_p, 0) with u_p
     // from the FP64 cubic
     const R tp = turning_t<R>(H, M3);
-    const R ug = H.val_t(tp);
-    const double up = periastron64(s.M, (double)r.u0, (double)r.v0, (double)ug);
-    if (tp > R(0)) {
+    if (tp > R(0) && r.up == r.up) {
       const R hp = tp * h;
       pb = pa + hp;
-      un = R(up);
+      un = r.up;
       vn = R(0);
       fn = accel(M3, un);
       H.make(pa, hp, r.u, r.v, r.f, un, vn, fn);
@@ -227,13 +294,13 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
   int bt = -1;
   R bp = R(0);
   unsigned bid = 0;
-  if (un >= R(s.u_capt)) consider<R>(EV_CAPT, pa + H.h * hermite_root<R>(H, R(s.u_capt), R(0), R(1)), 0u, bt, bp, bid);
+  if (un >= S.u_capt) consider<R>(EV_CAPT, pa + H.h * hermite_root<R>(H, S.u_capt, R(0), R(1)), 0u, bt, bp, bid);
   if (un <= R(0)) consider<R>(EV_ESC, pa + H.h * hermite_root<R>(H, R(0), R(0), R(1)), 0u, bt, bp, bid);
   for (int it = 0; it < 8 && r.phi_node <= pb; ++it) {
     const R uk = H.u_at(r.phi_node);
     if (uk > R(0)) {
       const R rk = R(1) / uk;
-      if (rk >= R(s.r_in) && rk <= R(s.r_out)) {
+      if (rk >= S.r_in && rk <= S.r_out) {
         consider<R>(EV_DISK, r.phi_node, 0u, bt, bp, bid);
         break;
       }
@@ -248,7 +315,7 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
       R ph;
       if (sphere_entry<R>(s, r, k, H, pa, pb, &ph)) consider<R>(EV_SPHERE, ph, (unsigned)k, bt, bp, bid);
     }
-    r.phi_sph = next_sphere_window<R>(s, r, pb);
+    r.phi_sph = next_sphere_window<R>(r, pb);
   }
   if (bt < 0) return false;
   hit.phi = bp;
@@ -264,17 +331,16 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
 // One attempted step.  Returns true when the ray ended (hit filled in).
 template <typename R, int MODE>
 __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit, LocalStats& st) {
-  const R M3 = R(p.s.M3);
-  const R rtol = R(MODE == MODE_BAND64 ? p.rtol64 : p.rtol);
-  const R atol = R(MODE == MODE_BAND64 ? p.atol64 : p.atol);
+  const SceneR<R>& S = SR<R>(p.s);
+  const TolR<R>& tol = TolPick<R, MODE>::get(p);
   R un, vn, fn, err2;
-  dp5_attempt<R>(M3, r.u, r.v, r.f, r.h, rtol, atol, un, vn, fn, err2);
+  dp5_attempt<R>(S.M3, r.u, r.v, r.f, r.h, tol.rtol, tol.atol, un, vn, fn, err2);
   r.steps++;
   st.c[ST_STEPS]++;
   if (sizeof(R) == 8) st.c[ST_STEPS64]++;
   const R h = r.h;
   r.h = h * step_factor<R>(err2);
-  if (MODE != MODE_BAND64) r.h = m_min(r.h, R(p.h_max));
+  r.h = m_min(r.h, tol.h_max);
   if (!(err2 <= R(1))) {
     st.c[ST_REJ]++;
     if (r.steps >= p.max_steps) {
@@ -284,13 +350,13 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     return false;
   }
   R pb = r.phi + h;
-  bool slow = (un <= R(0)) | (un >= R(p.s.u_capt)) | (pb >= r.phi_node) | (pb >= r.phi_sph);
+  bool slow = (un <= R(0)) | (un >= S.u_capt) | (pb >= r.phi_node) | (pb >= r.phi_sph);
   bool peri = false;
   if (MODE == MODE_MIXED) {
     peri = p.peri_reset && (r.v > R(0)) && (vn <= R(0)) && !(r.aux & kAuxPeriDone);
     slow |= peri;
   }
-  if (slow) {
+  if (__builtin_expect(slow, 0)) {
     st.c[ST_EVENTS]++;
     if (step_events<R, MODE>(p, r, un, vn, fn, pb, h, peri, hit, st)) return true;
   }
@@ -298,7 +364,7 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   r.v = vn;
   r.f = fn;
   r.phi = pb;
-  if (r.steps >= p.max_steps || pb >= R(p.phi_max)) {
+  if (r.steps >= p.max_steps || pb >= tol.phi_max) {
     hit.flags = BH_FLAG_STEP_LIMIT;
     return true;
   }
@@ -307,8 +373,12 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
 
 // Coherent pass: one 32-ray tile per warp grab, lanes in lock step, rays
 // over the step budget moved to the long-ray list.
+// Resident 256-thread blocks per SM the register allocation must allow:
+// 4 (64 registers) for the FP32 kernels, 2 for FP64.
+template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
+
 template <typename R, int MODE, typename OutR>
-__global__ void __launch_bounds__(256) k_coherent(Params p) {
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
   const int lane = threadIdx.x & 31;
   LocalStats st;
   st.zero();
@@ -367,9 +437,9 @@ __device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ra
     r.v = sp->v;
     r.phi = sp->phi;
     r.h = sp->h;
-    r.f = accel(R(p.s.M3), r.u);
+    r.f = accel(SR<R>(p.s).M3, r.u);
     for (int it = 0; it < 64 && r.phi_node <= r.phi; ++it) r.phi_node += Num<R>::pi;
-    if (r.sph_mask) r.phi_sph = next_sphere_window<R>(p.s, r, r.phi);
+    if (r.sph_mask) r.phi_sph = next_sphere_window<R>(r, r.phi);
   }
   return true;
 }
@@ -377,7 +447,7 @@ __device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ra
 // Long-ray pass: every lane refills on its own from a list (saved long
 // rays, or FP64 band rays), warp-aggregated: one atomic per refill round.
 template <typename R, int MODE, typename OutR, bool FROM_SPILL>
-__global__ void __launch_bounds__(256) k_longrays(Params p) {
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_longrays(const __grid_constant__ Params p) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned long long* next = FROM_SPILL ? &p.ws->long_next : &p.ws->band_next;
@@ -390,7 +460,8 @@ __global__ void __launch_bounds__(256) k_longrays(Params p) {
   bool active = false, exhausted = false;
   for (long long guard = 0; guard < (1ll << 40); ++guard) {
     if (!exhausted) {
-      const unsigned need = __ballot_sync(kFull, !active);
+      const int lanes = FROM_SPILL ? 32 : p.band_lanes;
+      const unsigned need = __ballot_sync(kFull, !active && lane < lanes);
       if (need) {
         unsigned long long base = 0;
         if (lane == 0) {
@@ -466,15 +537,36 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
-  } else {
+  } else if (!ls.side || !p.band_bits) {
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
     auto k2 = k_longrays<float, MODE_MIXED, float, true>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
+    // FP64 band rays are few: one warp per block and one block per SM
+    // sub-partition, so every warp gets an FP64 unit of its own
     auto k3 = k_longrays<double, MODE_BAND64, float, false>;
-    k3<<<grid_of(k3), block, 0, stream>>>(p);
+    k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
+    rec(3);
+  } else {
+    // band pre-pass, then the FP64 band pass on the high-priority side
+    // stream concurrently with the FP32 coherent and long-ray passes
+    k_band_scan<<<ls.num_sms * 8, 256, 0, stream>>>(p);
+    cudaEventRecord(ls.fork, stream);
+    cudaStreamWaitEvent(ls.side, ls.fork, 0);
+    if (ls.band_ev && ls.band_ev[0]) cudaEventRecord(ls.band_ev[0], ls.side);
+    auto k3 = k_longrays<double, MODE_BAND64, float, false>;
+    k3<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
+    if (ls.band_ev && ls.band_ev[1]) cudaEventRecord(ls.band_ev[1], ls.side);
+    cudaEventRecord(ls.join, ls.side);
+    auto k1 = k_coherent<float, MODE_MIXED, float>;
+    k1<<<grid_of(k1), block, 0, stream>>>(p);
+    rec(1);
+    auto k2 = k_longrays<float, MODE_MIXED, float, true>;
+    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    rec(2);
+    cudaStreamWaitEvent(stream, ls.join, 0);
     rec(3);
   }
   return cudaGetLastError();

@@ -11,6 +11,12 @@ struct LaunchShape {
   int num_sms;        // streaming multiprocessors of the device
   int block;          // threads per block
   int blocks_per_sm;  // 0: the occupancy limit of each kernel
+  // MIXED only: side stream (high priority) and fork / join events that run
+  // the FP64 band pass next to the FP32 passes; band_ev[0..1] time it.
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t* band_ev = nullptr;
+  int band_warps = 4;  // band-pass warps per SM (one-warp blocks)
 };
 
 // Launch the kernels of one render (coherent pass, long-ray pass and, in

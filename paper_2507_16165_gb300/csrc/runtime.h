@@ -34,16 +34,23 @@ struct bh_scene {
   size_t stage_rgba_cap = 0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t band_ev[2] = {nullptr, nullptr};
+  cudaStream_t side = nullptr;               // FP64 band pass (MIXED)
+  cudaEvent_t fork = nullptr, join = nullptr;
+  unsigned* d_bits = nullptr;                // band bitmap, one bit per queue slot
+  size_t bits_cap = 0;
   bool timed = false;
+  bool band_used = false;  // last render ran the side-stream band pass
   SurrogateState* surr = nullptr;
 };
 
 // Resolved options of one render.
 struct RenderConfig {
   int mode;
-  double rtol, atol, band, phi_max, h_max;
+  double rtol, atol, band, band_rtol, phi_max, h_max;
   int max_steps;
   int block, blocks_per_sm, tile_w, tile_h, budget;
+  int band_lanes, band_warps;
   int peri_reset;
   unsigned long long abort_after;
 };
@@ -51,6 +58,7 @@ struct RenderConfig {
 // Launch shape picked by the autotuner (or the built-in default).
 struct TunedShape {
   int block, blocks_per_sm, tile_w, tile_h, budget;
+  int band_lanes, band_warps;  // MIXED FP64 band pass: lanes per warp, warps per SM
 };
 
 class DeviceGuard {
@@ -71,6 +79,7 @@ int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
 RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o);
 void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long long n_queue,
                  long long n_rays, void* dirs, uint16_t* flags, uint32_t* rgba, bhk::Params* out);
+void fill_tolerances(bhk::Params& p);
 int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                   void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts);
 

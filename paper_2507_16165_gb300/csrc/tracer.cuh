@@ -42,7 +42,10 @@ __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
 __device__ __forceinline__ double m_ceil(double x) { return ceil(x); }
 __device__ __forceinline__ float m_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double m_rcp(double x) { return 1.0 / x; }
+// double reciprocal through single precision: only the error norm uses it,
+// where a relative error of 1e-7 in err^2 cannot change an accept decision
+// except within 1e-7 of the threshold
+__device__ __forceinline__ double m_rcp(double x) { return (double)__frcp_rn((float)x); }
 
 template <typename R> struct Num;
 template <> struct Num<float> {
@@ -271,8 +274,10 @@ struct Ray {
   R e1x, e1y, e1z, e2x, e2y, e2z;  // plane basis
   R phi_node;            // next disk node angle (> phi), or +inf
   R phi_sph;             // next sphere-window start, or +inf
-  R u0, v0;              // initial state (for the periastron reset)
+  R up;                  // periastron u of the orbit (MIXED reset), NaN if none
   unsigned sph_mask;     // spheres whose in-plane circle is non-empty
+  float wc[kMaxSph];     // angular window of each such sphere: centre ...
+  float wd[kMaxSph];     // ... and half-width (rad), from the set-up
   int steps;             // attempted steps
   int out;               // output pixel index
   unsigned aux;          // BAND / FP64 provenance bits, periastron-done bit
@@ -291,49 +296,56 @@ struct Hit {
 // Camera ray through pixel (px, py) (pixel centres, row 0 at the top).
 template <typename R>
 __device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3], R d[3]) {
-  const R sx = (R(2) * (R(px) + R(0.5)) / R(c.w) - R(1)) * R(c.sx);
-  const R sy = (R(1) - R(2) * (R(py) + R(0.5)) / R(c.h)) * R(c.sy);
+  const CamR<R>& C = CR<R>(c);
+  const R sx = (R(2) * (R(px) + R(0.5)) / R(c.w) - R(1)) * C.sx;
+  const R sy = (R(1) - R(2) * (R(py) + R(0.5)) / R(c.h)) * C.sy;
   R dd[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    P[k] = R(c.pos[k]);
-    dd[k] = R(c.fwd[k]) + sx * R(c.right[k]) + sy * R(c.up[k]);
+    P[k] = C.pos[k];
+    dd[k] = C.fwd[k] + sx * C.right[k] + sy * C.up[k];
   }
   const R inv = R(1) / m_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = dd[k] * inv;
 }
 
-// Angular window [ws, we] of sphere k in the ray's plane: the directions
-// from the hole that meet the sphere's in-plane circle, the first one whose
-// end lies at or after phi_from.  Evaluated in single precision for both
-// arithmetic types (it only gates the exact test) and widened by 1e-4 rad.
+// Angular window [phi_c - dphi, phi_c + dphi] of sphere k in the ray's
+// plane: the directions from the hole that meet the sphere's in-plane
+// circle.  Evaluated once per ray in single precision for both arithmetic
+// types (it only gates the exact test) and widened by 1e-4 rad.
 template <typename R>
-__device__ __forceinline__ float sphere_window(const SceneK& s, const Ray<R>& r, int k,
-                                               float phi_from, float* we) {
-  const float c0 = (float)s.c[k][0], c1 = (float)s.c[k][1], c2 = (float)s.c[k][2];
+__device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, int k) {
+  const float c0 = s.f.c[k][0], c1 = s.f.c[k][1], c2 = s.f.c[k][2];
   const float cx = c0 * (float)r.e1x + c1 * (float)r.e1y + c2 * (float)r.e1z;
   const float cy = c0 * (float)r.e2x + c1 * (float)r.e2y + c2 * (float)r.e2z;
   const float rho2 = cx * cx + cy * cy;
-  const float rp2 = fmaxf(0.0f, (float)(s.R[k] * s.R[k]) - ((float)s.c2[k] - rho2));
+  const float rp2 = fmaxf(0.0f, s.f.rad[k] * s.f.rad[k] - (s.f.c2[k] - rho2));
   float pc = atan2f(cy, cx);
   if (pc < 0.0f) pc += 6.28318530717958647692f;
-  const float dp = asinf(fminf(1.0f, sqrtf(rp2 / rho2))) + 1e-4f;
+  r.wc[k] = pc;
+  r.wd[k] = asinf(fminf(1.0f, sqrtf(rp2 / rho2))) + 1e-4f;
+}
+
+// The first window of sphere k whose end lies at or after phi_from:
+// returns its start, *we its end.
+template <typename R>
+__device__ __forceinline__ float sphere_window(const Ray<R>& r, int k, float phi_from, float* we) {
+  const float pc = r.wc[k], dp = r.wd[k];
   const float m = ceilf((phi_from - pc - dp) * 0.15915494309189535f);
-  const float ws = pc - dp + 6.28318530717958647692f * m;
   *we = pc + dp + 6.28318530717958647692f * m;
-  return ws;
+  return pc - dp + 6.28318530717958647692f * m;
 }
 
 template <typename R>
-__device__ __forceinline__ R next_sphere_window(const SceneK& s, const Ray<R>& r, R phi_from) {
+__device__ __forceinline__ R next_sphere_window(const Ray<R>& r, R phi_from) {
   float best = INFINITY;
   unsigned m = r.sph_mask;
   while (m) {
     const int k = __ffs(m) - 1;
     m &= m - 1;
     float we;
-    best = fminf(best, sphere_window(s, r, k, (float)phi_from, &we));
+    best = fminf(best, sphere_window(r, k, (float)phi_from, &we));
   }
   return R(best);
 }
@@ -363,22 +375,21 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
   r.e2y = nz * r.e1x - nx * r.e1z;
   r.e2z = nx * r.e1y - ny * r.e1x;
   const R sin_a = d[0] * r.e2x + d[1] * r.e2y + d[2] * r.e2z;
-  const R M = R(s.M);
+  const SceneR<R>& S = SR<R>(s);
+  const R M = S.M;
   const R u0 = ir;
   const R cot = cos_a / sin_a;
   R b;
   if (s.ic == 0) {
     b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * ir);
-    r.v0 = -u0 * cot * m_sqrt(R(1) - R(2) * M * u0);
+    r.v = -u0 * cot * m_sqrt(R(1) - R(2) * M * u0);
   } else {
     b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * sin_a * sin_a * ir);
-    r.v0 = -u0 * cot;
+    r.v = -u0 * cot;
   }
   *b_out = b;
-  r.u0 = u0;
   r.u = u0;
-  r.v = r.v0;
-  r.f = accel(R(s.M3), u0);
+  r.f = accel(S.M3, u0);
   r.phi = R(0);
   // disk nodes: z(phi) ~ cos(phi) e1z + sin(phi) e2z
   r.phi_node = R(INFINITY);
@@ -394,11 +405,20 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
   // spheres cut by the plane
   unsigned mask = 0;
   for (int k = 0; k < s.n_sph; ++k) {
-    const R sd = nx * R(s.c[k][0]) + ny * R(s.c[k][1]) + nz * R(s.c[k][2]);
-    if (m_abs(sd) < R(s.R[k])) mask |= 1u << k;
+    const R sd = nx * S.c[k][0] + ny * S.c[k][1] + nz * S.c[k][2];
+    if (m_abs(sd) < S.rad[k]) mask |= 1u << k;
   }
   r.sph_mask = mask;
-  r.phi_sph = mask ? next_sphere_window(s, r, R(0)) : R(INFINITY);
+  r.phi_sph = R(INFINITY);
+  if (mask) {
+    unsigned m = mask;
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1;
+      sphere_window_setup(s, r, k);
+    }
+    r.phi_sph = next_sphere_window(r, R(0));
+  }
   return 0;
 }
 
@@ -420,15 +440,16 @@ template <typename R>
 __device__ bool sphere_entry(const SceneK& s, const Ray<R>& r, int k, const Hermite<R>& H,
                              R pa, R pb, R* phi_hit) {
   float wef;
-  const float wsf = sphere_window(s, r, k, (float)pa, &wef);
+  const float wsf = sphere_window(r, k, (float)pa, &wef);
   if (R(wsf) > pb || R(wef) < pa) return false;
   R lo = m_max(pa, R(wsf)), hi = m_min(pb, R(wef));
   if (!(hi > lo)) return false;
-  const R c0 = R(s.c[k][0]), c1 = R(s.c[k][1]), c2 = R(s.c[k][2]);
+  const SceneR<R>& S = SR<R>(s);
+  const R c0 = S.c[k][0], c1 = S.c[k][1], c2 = S.c[k][2];
   const R cx = c0 * r.e1x + c1 * r.e1y + c2 * r.e1z;
   const R cy = c0 * r.e2x + c1 * r.e2y + c2 * r.e2z;
-  const R K = R(s.K[k]);
-  const R rp2 = R(s.R[k]) * R(s.R[k]) - (R(s.c2[k]) - (cx * cx + cy * cy));
+  const R K = S.K[k];
+  const R rp2 = S.rad[k] * S.rad[k] - (S.c2[k] - (cx * cx + cy * cy));
   if (!(rp2 > R(0))) return false;
   const R ulo = H.u_at(lo), uhi = H.u_at(hi);
   if (ulo > R(0) && uhi > R(0)) {
@@ -445,7 +466,7 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<R>& r, int k, const Herm
     const R dx = qx - t * bx, dy = qy - t * by;
     const R q = m_max(ulo, uhi) / m_min(ulo, uhi);
     const R hh = hi - lo;
-    const R margin = R(0.47) * R(s.M3) * q * q * hh * hh + R(1e-6);
+    const R margin = R(0.47) * S.M3 * q * q * hh * hh + R(1e-6);
     const R reach = m_sqrt(rp2) + margin;
     if (m_fma(dx, dx, dy * dy) > reach * reach) return false;
   }
@@ -566,9 +587,13 @@ __device__ __forceinline__ void store_ray(const Params& p, int out, OutR th, Out
   if (p.rgba) p.rgba[out] = rgba;
 }
 
-// Map a terminated ray back to 3-D, shade it and store it.
+// Map a terminated ray back to 3-D, shade it and store it.  The map-back
+// and shading run in the output precision OutR: an FP64 ray of the MIXED
+// band is reduced to phi mod 2 pi in FP64 and finished in FP32, as its
+// directions are stored in FP32.
 template <typename R, typename OutR>
 __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) {
+  using T = OutR;
   const SceneK& s = p.s;
   const unsigned fl = hit.flags & 0xFFu;
   const unsigned flags = hit.flags | (r.aux & 0xFFu);
@@ -576,37 +601,42 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) 
     store_ray<OutR>(p, r.out, OutR(NAN), OutR(NAN), flags, 255u << 24);
     return;
   }
-  R sp, cp;
-  m_sincos(hit.phi, &sp, &cp);
-  const R dx = cp * r.e1x + sp * r.e2x;
-  const R dy = cp * r.e1y + sp * r.e2y;
-  const R dz = cp * r.e1z + sp * r.e2z;
-  R th, ph;
+  R phr = hit.phi;
+  if (sizeof(T) < sizeof(R)) phr -= Num<R>::two_pi * m_floor(phr * R(0.15915494309189535));
+  T sp, cp;
+  m_sincos(T(phr), &sp, &cp);
+  const T e1x = T(r.e1x), e1y = T(r.e1y), e1z = T(r.e1z);
+  const T e2x = T(r.e2x), e2y = T(r.e2y), e2z = T(r.e2z);
+  const T dx = cp * e1x + sp * e2x;
+  const T dy = cp * e1y + sp * e2y;
+  const T dz = cp * e1z + sp * e2z;
+  T th, ph;
   dir_angles(dx, dy, dz, &th, &ph);
   unsigned rgba;
   if (fl == BH_FLAG_ESC) {
-    rgba = sky_rgba<R>(s.seed, th, ph);
+    rgba = sky_rgba<T>(s.seed, th, ph);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
-    const float t = exp2f(0.75f * __log2f((float)s.r_in / rr));
+    const float t = exp2f(0.75f * __log2f(s.f.r_in / rr));
     const float k = fmaf(0.7f, t, 0.3f);
     rgba = pack_rgba(k, fmaf(0.65f, t, 0.35f) * k, fmaf(0.9f * t, t, 0.1f) * k);
   } else {  // sphere
     const int id = (int)(hit.flags >> 8);
-    const R u = hit.u, v = hit.v;
-    const R iu = R(1) / u;
+    const T u = T(hit.u), v = T(hit.v);
+    const T iu = T(1) / u;
     // tangent d x/d phi scaled by u^2
-    R T[3] = {u * (-sp * r.e1x + cp * r.e2x) - v * dx, u * (-sp * r.e1y + cp * r.e2y) - v * dy,
-              u * (-sp * r.e1z + cp * r.e2z) - v * dz};
-    const R it = R(1) / m_sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
-    const R iR = R(1) / R(s.R[id]);
-    const R N0 = (dx * iu - R(s.c[id][0])) * iR, N1 = (dy * iu - R(s.c[id][1])) * iR,
-            N2 = (dz * iu - R(s.c[id][2])) * iR;
-    const float ndt = (float)(-(N0 * T[0] + N1 * T[1] + N2 * T[2]) * it);
+    const T T0 = u * (-sp * e1x + cp * e2x) - v * dx, T1 = u * (-sp * e1y + cp * e2y) - v * dy,
+            T2 = u * (-sp * e1z + cp * e2z) - v * dz;
+    const T it = T(1) / m_sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+    const SceneR<T>& S = SR<T>(s);
+    const T iR = T(1) / S.rad[id];
+    const T N0 = (dx * iu - S.c[id][0]) * iR, N1 = (dy * iu - S.c[id][1]) * iR,
+            N2 = (dz * iu - S.c[id][2]) * iR;
+    const float ndt = (float)(-(N0 * T0 + N1 * T1 + N2 * T2) * it);
     const float lam = 0.25f + 0.75f * fmaxf(0.0f, ndt);
     rgba = pack_rgba(s.alb[id][0] * lam, s.alb[id][1] * lam, s.alb[id][2] * lam);
   }
-  store_ray<OutR>(p, r.out, OutR(th), OutR(ph), flags, rgba);
+  store_ray<OutR>(p, r.out, th, ph, flags, rgba);
 }
 
 }  // namespace bhk
