@@ -182,8 +182,9 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   if (MODE == MODE_MIXED) r.up = R(periastron64(p.s.f.M, float(r.u), float(r.v)));
   r.steps = 0;
   const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
-  r.h = initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol,
-                        d64 ? R(0.01) : m_min(R(1), tol.h_max));
+  // FP64 mirrors the oracle's starting step; FP32 starts at the step cap
+  // (the controller shrinks it when the first attempt is rejected)
+  r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01)) : tol.h_max;
   return true;
 }
 

@@ -37,6 +37,16 @@ __device__ __forceinline__ float m_acos(float x) { return acosf(x); }
 __device__ __forceinline__ double m_acos(double x) { return acos(x); }
 __device__ __forceinline__ float m_asin(float x) { return asinf(x); }
 __device__ __forceinline__ double m_asin(double x) { return asin(x); }
+// sin and cos for the map-back: Cody & Waite argument reduction by 2 pi with
+// a two-term split of 2 pi (float(2 pi) and its residual), then the hardware
+// approximation on [-pi, pi] (absolute error below 4e-7).  The FP64
+// overload is the accurate library routine.
+__device__ __forceinline__ void m_sincos_mapback(float x, float* s, float* c) {
+  const float k = rintf(x * 0.15915494309189535f);
+  const float r = fmaf(k, 1.7484555e-7f, fmaf(-k, 6.28318548202514648f, x));
+  __sincosf(r, s, c);
+}
+__device__ __forceinline__ void m_sincos_mapback(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
@@ -604,7 +614,7 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) 
   R phr = hit.phi;
   if (sizeof(T) < sizeof(R)) phr -= Num<R>::two_pi * m_floor(phr * R(0.15915494309189535));
   T sp, cp;
-  m_sincos(T(phr), &sp, &cp);
+  m_sincos_mapback(T(phr), &sp, &cp);
   const T e1x = T(r.e1x), e1y = T(r.e1y), e1z = T(r.e1z);
   const T e2x = T(r.e2x), e2y = T(r.e2y), e2z = T(r.e2z);
   const T dx = cp * e1x + sp * e2x;
