@@ -212,6 +212,41 @@ int bh_scene_sync(const bh_scene *scene);
 /* Statistics of the scene's last render (synchronises its stream). */
 int bh_render_stats(const bh_scene *scene, bh_stats *out);
 
+/* ---- batched launch in a CUDA graph, autotuning ------------------------
+ * One render of n_cams cameras (Sec. 3.2's scaling runs render many images;
+ * here many cameras of uneven resolution share one persistent launch
+ * sequence) captured once and replayed.  The graph owns a copy of the
+ * camera table; it renders into the output buffers given at creation and
+ * uses the scene's workspace, so graph launches and other renders on the
+ * same scene must not overlap.  Modes: FP64, FP32, MIXED.
+ * Errors: BH_E_INVALID, BH_E_NOMEM, BH_E_CUDA, BH_E_UNSUPPORTED. */
+typedef struct bh_graph bh_graph;
+int bh_graph_create(bh_scene *scene, const bh_camera *cams, int n_cams, const int *w,
+                    const int *h, void *out_dirs, uint16_t *out_flags, uint32_t *out_rgba8,
+                    const bh_render_opts *opts, bh_graph **out);
+/* Replay on a stream (a cudaStream_t); asynchronous. */
+int bh_graph_launch(bh_graph *graph, void *stream);
+void bh_graph_destroy(bh_graph *graph);
+
+typedef struct bh_tune_result {
+  int block_size, blocks_per_sm, tile_w, tile_h, budget; /* the fastest shape */
+  float ms_best;     /* its render time                                   */
+  float ms_default;  /* render time with the built-in default shape        */
+  int trials;        /* shapes timed                                       */
+} bh_tune_result;
+
+/* Time candidate launch shapes (block size, tile shape, step budget and, in
+ * MIXED, the resident blocks left to the band pass) on this workload -- each
+ * a full render into the given device buffers, synchronising the stream --
+ * and keep the fastest for the scene's device and this mode: later renders
+ * and graphs whose opts leave those fields 0 use it.  Modes: FP64, FP32,
+ * MIXED.  Errors as bh_render, plus BH_E_UNSUPPORTED. */
+int bh_autotune(bh_scene *scene, const bh_camera *cams, int n_cams, const int *w, const int *h,
+                void *out_dirs, uint16_t *out_flags, uint32_t *out_rgba8,
+                const bh_render_opts *opts, bh_tune_result *out);
+/* Forget every tuned shape (back to the built-in defaults). */
+int bh_autotune_reset(void);
+
 /* ---- render without allocating ----------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc: hosts that give all device memory to their own

@@ -23,7 +23,9 @@ from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # no
 
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
            "bh_camera_set", "bh_render", "bh_render_host", "bh_scene_sync",
-           "bh_render_stats", "bh_render_noalloc", "Scene", "render_opts", "render_workload"]
+           "bh_render_stats", "bh_render_noalloc", "bh_graph_create", "bh_graph_launch",
+           "bh_graph_destroy", "bh_autotune", "bh_autotune_reset", "Scene", "render_opts",
+           "render_workload"]
 
 
 def bh_version() -> int:
@@ -145,6 +147,43 @@ def bh_render_noalloc(desc: _capi.bh_scene_desc, cams, w, h, out_dirs, out_flags
     check(_capi.lib().bh_render_noalloc(ctypes.byref(desc), _cams_array(cams), n, W, H,
                                         _ptr(out_dirs), _ptr(out_flags), _ptr(out_rgba8),
                                         ctypes.byref(opts)), "bh_render_noalloc")
+
+
+def bh_graph_create(scene: int, cams, w, h, out_dirs, out_flags, out_rgba8, opts) -> int:
+    """Capture one render into a CUDA graph; returns the bh_graph handle."""
+    n = len(cams)
+    W = (ctypes.c_int * n)(*[int(x) for x in w])
+    H = (ctypes.c_int * n)(*[int(x) for x in h])
+    g = ctypes.c_void_p()
+    check(_capi.lib().bh_graph_create(scene, _cams_array(cams), n, W, H, _ptr(out_dirs),
+                                      _ptr(out_flags), _ptr(out_rgba8), ctypes.byref(opts),
+                                      ctypes.byref(g)), "bh_graph_create")
+    return g.value
+
+
+def bh_graph_launch(graph: int, stream=None) -> None:
+    check(_capi.lib().bh_graph_launch(graph, _stream_ptr(stream)), "bh_graph_launch")
+
+
+def bh_graph_destroy(graph: int) -> None:
+    if graph:
+        _capi.lib().bh_graph_destroy(graph)
+
+
+def bh_autotune(scene: int, cams, w, h, out_dirs, out_flags, out_rgba8, opts) -> dict:
+    """Time launch shapes on this workload; the fastest becomes the default."""
+    n = len(cams)
+    W = (ctypes.c_int * n)(*[int(x) for x in w])
+    H = (ctypes.c_int * n)(*[int(x) for x in h])
+    res = _capi.bh_tune_result()
+    check(_capi.lib().bh_autotune(scene, _cams_array(cams), n, W, H, _ptr(out_dirs),
+                                  _ptr(out_flags), _ptr(out_rgba8), ctypes.byref(opts),
+                                  ctypes.byref(res)), "bh_autotune")
+    return {name: getattr(res, name) for name, _ in _capi.bh_tune_result._fields_}
+
+
+def bh_autotune_reset() -> None:
+    check(_capi.lib().bh_autotune_reset(), "bh_autotune_reset")
 
 
 def bh_scene_sync(scene: int) -> None:

@@ -66,6 +66,13 @@ class bh_stats(ctypes.Structure):
                                     ("kernel_ms", ctypes.c_float * 4)]
 
 
+class bh_tune_result(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
+                ("ms_best", ctypes.c_float), ("ms_default", ctypes.c_float),
+                ("trials", ctypes.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -86,6 +93,13 @@ SIGNATURES = [
                             ctypes.POINTER(bh_render_opts)]),
     ("bh_scene_sync", _I, [_P]),
     ("bh_render_stats", _I, [_P, ctypes.POINTER(bh_stats)]),
+    ("bh_graph_create", _I, [_P, ctypes.POINTER(bh_camera), _I, _P, _P, _P, _P, _P,
+                             ctypes.POINTER(bh_render_opts), ctypes.POINTER(_P)]),
+    ("bh_graph_launch", _I, [_P, _P]),
+    ("bh_graph_destroy", None, [_P]),
+    ("bh_autotune", _I, [_P, ctypes.POINTER(bh_camera), _I, _P, _P, _P, _P, _P,
+                         ctypes.POINTER(bh_render_opts), ctypes.POINTER(bh_tune_result)]),
+    ("bh_autotune_reset", _I, []),
     ("bh_render_noalloc", _I, [ctypes.POINTER(bh_scene_desc), ctypes.POINTER(bh_camera), _I,
                                _P, _P, _P, _P, _P, ctypes.POINTER(bh_render_opts)]),
 ]

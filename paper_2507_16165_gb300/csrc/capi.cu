@@ -296,27 +296,33 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   return c;
 }
 
-int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
-                  void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts) {
+// Host-side preparation of one render: resolve options, build the camera
+// table (uploaded to cams_dev, or to the scene's table when null), size the
+// scene workspace and fill the kernel parameters and launch shape.
+int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                   void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
+                   cudaStream_t upload_stream, CamK* cams_dev, PreparedRender* out) {
   const RenderConfig cfg = resolve_config(sc, opts);
-  if (cfg.mode == BH_MODE_SURROGATE) return surrogate_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, cfg);
   long long n_queue = 0, n_rays = 0;
   int rc = build_cameras(sc, cams, n_cams, w, h, cfg.tile_w, cfg.tile_h, &n_queue, &n_rays);
   if (rc) return rc;
-  cudaStream_t stream = (cudaStream_t)opts->stream;
-  cudaError_t e = grow(&sc->d_cams, &sc->cams_cap, (size_t)n_cams);
+  cudaError_t e = cudaSuccess;
+  if (!cams_dev) {
+    e = grow(&sc->d_cams, &sc->cams_cap, (size_t)n_cams);
+    cams_dev = sc->d_cams;
+  }
   if (e == cudaSuccess) e = grow(&sc->d_band, &sc->band_cap, (size_t)n_queue);
   const size_t spill_bytes = (cfg.mode == BH_MODE_FP64 ? sizeof(Spill<double>) : sizeof(Spill<float>));
   if (e == cudaSuccess) e = grow(&sc->d_spill, &sc->spill_cap, (size_t)n_queue * spill_bytes);
   if (e == cudaSuccess && cfg.mode == BH_MODE_MIXED)
     e = grow(&sc->d_bits, &sc->bits_cap, (size_t)(n_queue / 32 + 1));
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: workspace allocation");
-  e = cudaMemcpyAsync(sc->d_cams, sc->h_cams.data(), n_cams * sizeof(CamK), cudaMemcpyHostToDevice,
-                      stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
-  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: upload");
-  Params p;
+  e = cudaMemcpyAsync(cams_dev, sc->h_cams.data(), n_cams * sizeof(CamK), cudaMemcpyHostToDevice,
+                      upload_stream);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: camera upload");
+  Params& p = out->p;
   fill_params(sc, cfg, n_cams, n_queue, n_rays, dirs, flags, rgba, &p);
+  p.cams = cams_dev;
   LaunchShape ls{sc->num_sms, cfg.block, cfg.blocks_per_sm};
   if (cfg.mode == BH_MODE_MIXED) {
     p.band_bits = sc->d_bits;
@@ -326,12 +332,36 @@ int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
     ls.band_ev = sc->band_ev;
     ls.band_warps = cfg.band_warps;
   }
-  const int kmode = cfg.mode == BH_MODE_FP64 ? MODE_FP64 : cfg.mode == BH_MODE_FP32 ? MODE_FP32 : MODE_MIXED;
-  e = launch_render(p, kmode, ls, stream, sc->ev);
+  out->ls = ls;
+  out->kmode = cfg.mode == BH_MODE_FP64 ? MODE_FP64 : cfg.mode == BH_MODE_FP32 ? MODE_FP32 : MODE_MIXED;
+  out->mode = cfg.mode;
+  return BH_OK;
+}
+
+// Work of one prepared render on `stream`: clear the workspace, launch the
+// passes.  Also what a CUDA graph of the render captures.
+int enqueue_render(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
+  if (e == cudaSuccess) e = launch_render(pr.p, pr.kmode, pr.ls, stream, sc->ev);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: launch");
+  return BH_OK;
+}
+
+int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                  void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts) {
+  if (opts->mode == BH_MODE_SURROGATE) {
+    const RenderConfig cfg = resolve_config(sc, opts);
+    return surrogate_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, cfg);
+  }
+  cudaStream_t stream = (cudaStream_t)opts->stream;
+  PreparedRender pr;
+  int rc = prepare_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, stream, nullptr, &pr);
+  if (rc) return rc;
+  rc = enqueue_render(sc, pr, stream);
+  if (rc) return rc;
   sc->last_stream = stream;
   sc->timed = true;
-  sc->band_used = (cfg.mode == BH_MODE_MIXED);
+  sc->band_used = (pr.mode == BH_MODE_MIXED);
   return BH_OK;
 }
 
@@ -469,6 +499,7 @@ extern "C" int bh_render_stats(const bh_scene* scene, bh_stats* out) {
     }
     float tot = 0.0f;
     if (cudaEventElapsedTime(&tot, scene->ev[0], scene->ev[3]) == cudaSuccess) out->kernel_ms[3] = tot;
+    cudaGetLastError();  // an event that never completed only leaves a time at 0
   }
   return BH_OK;
 }

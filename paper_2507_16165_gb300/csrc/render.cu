@@ -513,13 +513,26 @@ static int occupancy(K kernel, int block) {
 
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
                           cudaEvent_t* ev) {
+  // a failure left by earlier, unrelated runtime calls is not this launch's
+  cudaGetLastError();
+  // while the stream is captured into a graph, timing events must be
+  // recorded as external event nodes to carry timestamps at replay
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(stream, &cap);
+  const bool capturing = cap == cudaStreamCaptureStatusActive;
+  auto record = [&](cudaEvent_t e, cudaStream_t s) {
+    if (capturing)
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s);
+  };
   const int block = ls.block;
   auto grid_of = [&](auto kernel) {
     const int per_sm = ls.blocks_per_sm > 0 ? ls.blocks_per_sm : occupancy(kernel, block);
     return ls.num_sms * per_sm;
   };
   auto rec = [&](int i) {
-    if (ev && ev[i]) cudaEventRecord(ev[i], stream);
+    if (ev && ev[i]) record(ev[i], stream);
   };
   rec(0);
   if (mode == MODE_FP64) {
@@ -556,10 +569,10 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k_band_scan<<<ls.num_sms * 8, 256, 0, stream>>>(p);
     cudaEventRecord(ls.fork, stream);
     cudaStreamWaitEvent(ls.side, ls.fork, 0);
-    if (ls.band_ev && ls.band_ev[0]) cudaEventRecord(ls.band_ev[0], ls.side);
+    if (ls.band_ev && ls.band_ev[0]) record(ls.band_ev[0], ls.side);
     auto k3 = k_longrays<double, MODE_BAND64, float, false>;
     k3<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
-    if (ls.band_ev && ls.band_ev[1]) cudaEventRecord(ls.band_ev[1], ls.side);
+    if (ls.band_ev && ls.band_ev[1]) record(ls.band_ev[1], ls.side);
     cudaEventRecord(ls.join, ls.side);
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);

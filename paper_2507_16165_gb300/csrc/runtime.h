@@ -7,6 +7,7 @@
 
 #include "bh.h"
 #include "bh_types.cuh"
+#include "render.h"
 
 constexpr int kMaxCameras = 4096;
 
@@ -80,6 +81,18 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o);
 void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long long n_queue,
                  long long n_rays, void* dirs, uint16_t* flags, uint32_t* rgba, bhk::Params* out);
 void fill_tolerances(bhk::Params& p);
+
+// A render prepared on the host: kernel parameters and launch shape.
+struct PreparedRender {
+  bhk::Params p;
+  bhk::LaunchShape ls;
+  int kmode;  // bhk::Mode of the main pass
+  int mode;   // BH_MODE_*
+};
+int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                   void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
+                   cudaStream_t upload_stream, bhk::CamK* cams_dev, PreparedRender* out);
+int enqueue_render(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream);
 int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                   void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts);
 
