@@ -42,18 +42,21 @@ UNIT = "Mrays/s"
 FLOP_PER_STEP = 2 * 59 + 26 + 4
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9}
+STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9, "surrogate": 1e-3}
 # kernels one render launches: coherent + long-ray passes, and in MIXED the
 # band pre-pass and the FP64 band pass
-KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2}
+KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2, "surrogate": 4}
 
 
 def workload(form: str, size: int, name: str = "c3"):
-    """c3: the 4096^2 frame of one camera; c5: the 64-camera orbit sequence
-    (resolutions 256^2..2048^2, about 9e7 rays) rendered by one graph replay."""
+    """c3: the 4096^2 frame of one camera (the surrogate form renders the same
+    scene: config 4); c5: the 64-camera orbit sequence (resolutions
+    256^2..2048^2, about 9e7 rays) rendered by one graph replay."""
     if name == "c5":
         from dataclasses import replace
         return replace(W.config5(64), mode=form)
+    if form == "surrogate":
+        return W.config4(size)
     return W.config3(size, form)
 
 
@@ -258,6 +261,17 @@ def run_ours(args) -> None:
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band)
 
+    surrogate = None
+    if args.form == "surrogate":
+        # trained weights of the project (train_surrogate.py); training time
+        # is reported separately and is not part of the timed region
+        path = os.path.join(ROOT, "paper_2507_16165_gb300", "data", "surrogate_m1.bin")
+        bh.bh_surrogate_load(sc.handle, path)
+        try:
+            with open(os.path.splitext(path)[0] + ".json") as f:
+                surrogate = json.load(f)
+        except OSError:
+            surrogate = {"weights": path}
     graph = None
     tuned = None
     if args.workload == "c5":
@@ -384,10 +398,19 @@ def run_ours(args) -> None:
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_RENDER[args.form] * args.steps,
         "clocks": clk.summary(),
+        "surrogate_training": (dict({k: surrogate.get(k) for k in
+                                     ("samples", "n_valid", "epochs", "steps", "wall_s",
+                                      "train_ms", "label_ms", "val_rmse")},
+                                    calib_samples=surrogate["calibration"]["samples"],
+                                    calib_served_fraction=surrogate["calibration"]["served_fraction"],
+                                    served_bins=surrogate["calibration"]["served_bins"],
+                                    served_rays_fraction=stats["n_surrogate"] / n)
+                               if surrogate else None),
         "steps_per_ray": steps_all / args.steps / n,
         "wall_s": t_wall,
         "stats_last": {k: stats[k] for k in ("rays", "n_band", "n_long", "periastron", "n_capt",
-                                             "n_disk", "n_sphere", "n_esc")},
+                                             "n_disk", "n_sphere", "n_esc", "n_surrogate",
+                                             "n_fallback")},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -400,7 +423,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--form", choices=("mixed", "fp32", "fp64"), default="mixed")
+    ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate"), default="mixed")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--workload", choices=("c3", "c5"), default="c3")
     ap.add_argument("--no-e2e", action="store_true")

@@ -212,6 +212,110 @@ int bh_scene_sync(const bh_scene *scene);
 /* Statistics of the scene's last render (synchronises its stream). */
 int bh_render_stats(const bh_scene *scene, bh_stats *out);
 
+/* ---- MLP surrogate -------------------------------------------------------
+ * An MLP maps (b/M, r_obs/M, psi0) -- impact parameter, observer radius and
+ * the azimuth of the first disk node in the orbital plane -- to the
+ * deflection delta = phi_inf - alpha (alpha: the flat-space exit angle) and
+ * u b at the disk nodes psi0 and psi0 + pi: 3 inputs, 3 hidden layers of 64
+ * with SiLU, 3 outputs; BF16 operands with FP32 accumulation on the tensor
+ * cores for training and inference, FP32 master weights and Adam.  It is
+ * trained on labels the FP64 integrator computes, and calibrated on held-
+ * out samples: per bin of (ln(b - 3 sqrt 3 M), r_obs) the 99.9th-percentile
+ * error decides whether BH_MODE_SURROGATE may answer rays there.  Rays in
+ * the photon-sphere band, outside the training domain, in a failing bin, or
+ * whose orbital plane cuts a sphere are finished by the integrator.  There
+ * is no surrogate in the paper; the integrator is the judge of its error. */
+typedef struct bh_train_opts {
+  int epochs;            /* passes over the training samples (0: 20)       */
+  int batch;             /* samples per Adam step, multiple of 32 (0: 16384) */
+  double lr;             /* peak Adam learning rate, cosine decay (0: 2e-3) */
+  uint64_t seed;         /* weight initialisation and shuffling            */
+  double val_fraction;   /* held out for calibration (0: 0.05)             */
+  double err_threshold;  /* served bins: p99.9 |delta error| (0: 1e-3 rad) */
+  double r_err_threshold;/* and p99.9 relative crossing-radius error |dr|/r
+                            (0: 2e-3)                                       */
+  void *stream;          /* cudaStream_t                                   */
+} bh_train_opts;
+
+typedef struct bh_train_report {
+  int n_samples, n_valid, n_train, n_val, steps;
+  float final_loss;      /* mean training loss of the last epoch           */
+  float val_rmse[3];     /* held-out RMSE of the three normalised outputs  */
+  float served_fraction; /* held-out samples falling in served bins        */
+  float label_ms, train_ms, calib_ms;
+} bh_train_report;
+
+/* FP64 labels of bare orbits (device arrays of n): from r_obs with impact
+ * parameter b (units of M = mass), ingoing, static-observer initial state;
+ * phi_inf = escape azimuth, u_a / u_b = u at psi0 / psi0 + pi (continued
+ * past escape, where u < 0).  status: 0 ok, 1 no such ray from r_obs
+ * (b too large), 2 captured, 3 cap reached (labels NaN unless 0).
+ * Asynchronous on stream.  Errors: BH_E_INVALID, BH_E_CUDA. */
+int bh_surrogate_labels(double mass, int n, const double *b, const double *r_obs,
+                        const double *psi0, double *phi_inf, double *u_a, double *u_b,
+                        int *status, void *stream);
+
+/* Train the scene's surrogate on n host samples (b, r_obs, psi0) in units
+ * of M (labels from bh_surrogate_labels; invalid samples are dropped),
+ * calibrate it and keep it on the scene.  The loss is the mean squared
+ * error of the normalised outputs with the deflection term weighted by
+ * min(25, (10/b)^2), as its error in radians scales like 1/b.
+ * Synchronous.  report may be NULL.
+ * Errors: BH_E_INVALID, BH_E_NOMEM, BH_E_CUDA. */
+int bh_surrogate_train(bh_scene *scene, int n, const double *b, const double *r_obs,
+                       const double *psi0, const bh_train_opts *opts, bh_train_report *report);
+
+/* Recalibrate the scene's trained surrogate on n host samples (b, r_obs,
+ * psi0), units of M, that it was not trained on.  Each sample is labelled
+ * with the FP64 integrator (bh_surrogate_labels) and predicted by the
+ * network; samples are binned by the network's first feature
+ * (ln(b - 3 sqrt 3) normalised to [-1, 1], nb_lb bins) and by r_obs over
+ * [15, 100] M (nb_r bins).  Per bin the 99.9th percentile of the
+ * deflection error (rad) and of the relative disk-crossing radius error
+ * |dr| / r (true crossings within 2.5 M < r < 60 M) are taken; a bin is served when it
+ * holds >= 50 samples and both are within the thresholds.  The new table
+ * replaces the scene's (and is what bh_surrogate_save writes).
+ * Outputs (host, nb_lb * nb_r entries, bin = i_lb * nb_r + i_r, NULL to
+ * skip): p999_delta (rad), p999_r (relative), counts; served_fraction = share of valid
+ * samples in served bins.  Synchronous.
+ * Errors: BH_E_INVALID, BH_E_NO_SURROGATE, BH_E_NOMEM, BH_E_CUDA. */
+typedef struct bh_calib_opts {
+  int nb_lb;              /* bins over ln(b - 3 sqrt 3) (0: 32, <= 1024)   */
+  int nb_r;               /* bins over r_obs in [15, 100] M (0: 8, <= 1024) */
+  double err_threshold;   /* p99.9 |delta error| bound (0: 1e-3 rad)       */
+  double r_err_threshold; /* p99.9 relative crossing-radius bound (0: 2e-3) */
+  void *stream;           /* cudaStream_t                                  */
+} bh_calib_opts;
+int bh_surrogate_calibrate(bh_scene *scene, int n, const double *b, const double *r_obs,
+                           const double *psi0, const bh_calib_opts *opts, float *p999_delta,
+                           float *p999_r, int *counts, float *served_fraction);
+
+/* Copy the trained surrogate out (any pointer may be NULL): FP32 parameters
+ * (BH_MLP_NPARAM), calibration table (nb_lb * nb_r bytes).
+ * Errors: BH_E_INVALID, BH_E_NO_SURROGATE. */
+#define BH_MLP_NPARAM 10448
+int bh_surrogate_get(const bh_scene *scene, float *params, unsigned char *table, int *nb_lb,
+                     int *nb_r);
+
+/* Save / load the trained surrogate (parameters and calibration table; a
+ * file with magic, version, shapes and an FNV-1a checksum).
+ * Errors: BH_E_INVALID, BH_E_NO_SURROGATE, BH_E_IO, BH_E_CUDA. */
+int bh_surrogate_save(const bh_scene *scene, const char *path);
+int bh_surrogate_load(bh_scene *scene, const char *path);
+
+/* Diagnostics of the training kernels, on HOST arrays: one forward and
+ * backward pass of the MLP with FP32 parameters params (BH_MLP_NPARAM,
+ * row-major W[in][out] per layer, weights BF16-rounded on the device) over
+ * n samples (multiple of 32) of feature rows x[n][16] (12 used) and
+ * targets t[n][3]: outputs y[n][3], the gradient of the mean squared error
+ * over the 3 outputs with respect to every parameter, and the loss.
+ * Synchronous. */
+int bh_mlp_grad(const float *params, int n, const float *x, const float *t, float *y,
+                float *grad, float *loss, void *stream);
+/* The render's inference path (fragment-ordered BF16 weights, warp MLP) on
+ * host feature rows x[n][16] -> y[n][3].  Synchronous. */
+int bh_mlp_infer(const float *params, int n, const float *x, float *y, void *stream);
+
 /* ---- batched launch in a CUDA graph, autotuning ------------------------
  * One render of n_cams cameras (Sec. 3.2's scaling runs render many images;
  * here many cameras of uneven resolution share one persistent launch

@@ -24,7 +24,9 @@ from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # no
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
            "bh_camera_set", "bh_render", "bh_render_host", "bh_scene_sync",
            "bh_render_stats", "bh_render_noalloc", "bh_graph_create", "bh_graph_launch",
-           "bh_graph_destroy", "bh_autotune", "bh_autotune_reset", "Scene", "render_opts",
+           "bh_graph_destroy", "bh_autotune", "bh_autotune_reset", "bh_surrogate_labels",
+           "bh_surrogate_train", "bh_surrogate_calibrate", "bh_surrogate_get", "bh_surrogate_save", "bh_surrogate_load",
+           "bh_mlp_grad", "bh_mlp_infer", "Scene", "render_opts",
            "render_workload"]
 
 
@@ -184,6 +186,116 @@ def bh_autotune(scene: int, cams, w, h, out_dirs, out_flags, out_rgba8, opts) ->
 
 def bh_autotune_reset() -> None:
     check(_capi.lib().bh_autotune_reset(), "bh_autotune_reset")
+
+
+def bh_surrogate_labels(mass: float, b, r_obs, psi0, phi_inf, u_a, u_b, status, stream=None):
+    """FP64 integrator labels of bare orbits into device tensors."""
+    check(_capi.lib().bh_surrogate_labels(float(mass), int(b.numel()), _ptr(b), _ptr(r_obs),
+                                          _ptr(psi0), _ptr(phi_inf), _ptr(u_a), _ptr(u_b),
+                                          _ptr(status), _stream_ptr(stream)),
+          "bh_surrogate_labels")
+
+
+def bh_surrogate_train(scene: int, b, r_obs, psi0, stream=None, **kw) -> dict:
+    """Train and calibrate the scene's surrogate on host float64 arrays."""
+    import numpy as np
+    b = np.ascontiguousarray(b, np.float64)
+    r_obs = np.ascontiguousarray(r_obs, np.float64)
+    psi0 = np.ascontiguousarray(psi0, np.float64)
+    o = _capi.bh_train_opts()
+    o.stream = _stream_ptr(stream)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown training option {k}")
+        setattr(o, k, v)
+    rep = _capi.bh_train_report()
+    check(_capi.lib().bh_surrogate_train(scene, len(b), _ptr(b), _ptr(r_obs), _ptr(psi0),
+                                         ctypes.byref(o), ctypes.byref(rep)), "bh_surrogate_train")
+    out = {n: getattr(rep, n) for n, _ in _capi.bh_train_report._fields_}
+    out["val_rmse"] = list(rep.val_rmse)
+    return out
+
+
+def bh_surrogate_calibrate(scene: int, b, r_obs, psi0, nb_lb=32, nb_r=8, stream=None,
+                           **kw) -> dict:
+    """Recalibrate the scene's surrogate on held-out host float64 samples.
+
+    Returns per-bin arrays of shape (nb_lb, nb_r): p999_delta (rad),
+    p999_r (M), counts, served (bool), and served_fraction."""
+    import numpy as np
+    b = np.ascontiguousarray(b, np.float64)
+    r_obs = np.ascontiguousarray(r_obs, np.float64)
+    psi0 = np.ascontiguousarray(psi0, np.float64)
+    o = _capi.bh_calib_opts()
+    o.nb_lb, o.nb_r = int(nb_lb), int(nb_r)
+    o.stream = _stream_ptr(stream)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown calibration option {k}")
+        setattr(o, k, v)
+    nbin = o.nb_lb * o.nb_r
+    pd = np.empty(nbin, np.float32)
+    pr = np.empty(nbin, np.float32)
+    cnt = np.empty(nbin, np.int32)
+    served = ctypes.c_float()
+    check(_capi.lib().bh_surrogate_calibrate(scene, len(b), _ptr(b), _ptr(r_obs), _ptr(psi0),
+                                             ctypes.byref(o), _ptr(pd), _ptr(pr), _ptr(cnt),
+                                             ctypes.byref(served)), "bh_surrogate_calibrate")
+    _, table = bh_surrogate_get(scene)
+    shape = (o.nb_lb, o.nb_r)
+    return {"p999_delta": pd.reshape(shape), "p999_r": pr.reshape(shape),
+            "counts": cnt.reshape(shape), "served": table.astype(bool),
+            "served_fraction": served.value}
+
+
+def bh_surrogate_get(scene: int):
+    """(FP32 parameters, calibration table as an (nb_lb, nb_r) array)."""
+    import numpy as np
+    p = np.empty(_capi.BH_MLP_NPARAM, np.float32)
+    nb_lb, nb_r = ctypes.c_int(), ctypes.c_int()
+    check(_capi.lib().bh_surrogate_get(scene, None, None, ctypes.byref(nb_lb), ctypes.byref(nb_r)),
+          "bh_surrogate_get")
+    t = np.empty(nb_lb.value * nb_r.value, np.uint8)
+    check(_capi.lib().bh_surrogate_get(scene, _ptr(p), _ptr(t), None, None), "bh_surrogate_get")
+    return p, t.reshape(nb_lb.value, nb_r.value)
+
+
+def bh_surrogate_save(scene: int, path: str) -> None:
+    check(_capi.lib().bh_surrogate_save(scene, path.encode()), "bh_surrogate_save")
+
+
+def bh_surrogate_load(scene: int, path: str) -> None:
+    check(_capi.lib().bh_surrogate_load(scene, path.encode()), "bh_surrogate_load")
+
+
+def bh_mlp_grad(params, x, t, stream=None):
+    """(outputs, gradient, loss) of one forward/backward pass (host arrays)."""
+    import numpy as np
+    params = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    if x.ndim != 2 or x.shape[1] != 16:
+        raise ValueError("x must be n x 16 feature rows")
+    n = len(x)
+    y = np.empty((n, 3), np.float32)
+    g = np.empty(_capi.BH_MLP_NPARAM, np.float32)
+    loss = ctypes.c_float()
+    check(_capi.lib().bh_mlp_grad(_ptr(params), n, _ptr(x), _ptr(t), _ptr(y), _ptr(g),
+                                  ctypes.byref(loss), _stream_ptr(stream)), "bh_mlp_grad")
+    return y, g, loss.value
+
+
+def bh_mlp_infer(params, x, stream=None):
+    """Outputs of the render's inference MLP (host arrays)."""
+    import numpy as np
+    params = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    if x.ndim != 2 or x.shape[1] != 16:
+        raise ValueError("x must be n x 16 feature rows")
+    y = np.empty((len(x), 3), np.float32)
+    check(_capi.lib().bh_mlp_infer(_ptr(params), len(x), _ptr(x), _ptr(y), _stream_ptr(stream)),
+          "bh_mlp_infer")
+    return y
 
 
 def bh_scene_sync(scene: int) -> None:

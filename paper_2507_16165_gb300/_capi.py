@@ -66,6 +66,30 @@ class bh_stats(ctypes.Structure):
                                     ("kernel_ms", ctypes.c_float * 4)]
 
 
+class bh_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("val_fraction", ctypes.c_double),
+                ("err_threshold", ctypes.c_double), ("r_err_threshold", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class bh_train_report(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int), ("n_valid", ctypes.c_int), ("n_train", ctypes.c_int),
+                ("n_val", ctypes.c_int), ("steps", ctypes.c_int), ("final_loss", ctypes.c_float),
+                ("val_rmse", ctypes.c_float * 3), ("served_fraction", ctypes.c_float),
+                ("label_ms", ctypes.c_float), ("train_ms", ctypes.c_float),
+                ("calib_ms", ctypes.c_float)]
+
+
+class bh_calib_opts(ctypes.Structure):
+    _fields_ = [("nb_lb", ctypes.c_int), ("nb_r", ctypes.c_int),
+                ("err_threshold", ctypes.c_double), ("r_err_threshold", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+BH_MLP_NPARAM = 10448
+
+
 class bh_tune_result(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
@@ -100,6 +124,16 @@ SIGNATURES = [
     ("bh_autotune", _I, [_P, ctypes.POINTER(bh_camera), _I, _P, _P, _P, _P, _P,
                          ctypes.POINTER(bh_render_opts), ctypes.POINTER(bh_tune_result)]),
     ("bh_autotune_reset", _I, []),
+    ("bh_surrogate_labels", _I, [ctypes.c_double, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    ("bh_surrogate_train", _I, [_P, _I, _P, _P, _P, ctypes.POINTER(bh_train_opts),
+                                ctypes.POINTER(bh_train_report)]),
+    ("bh_surrogate_calibrate", _I, [_P, _I, _P, _P, _P, ctypes.POINTER(bh_calib_opts), _P, _P,
+                                    _P, _P]),
+    ("bh_surrogate_get", _I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("bh_surrogate_save", _I, [_P, ctypes.c_char_p]),
+    ("bh_surrogate_load", _I, [_P, ctypes.c_char_p]),
+    ("bh_mlp_grad", _I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    ("bh_mlp_infer", _I, [_P, _I, _P, _P, _P]),
     ("bh_render_noalloc", _I, [ctypes.POINTER(bh_scene_desc), ctypes.POINTER(bh_camera), _I,
                                _P, _P, _P, _P, _P, ctypes.POINTER(bh_render_opts)]),
 ]

@@ -120,6 +120,12 @@ struct Params {
   int* band_list;     // queue slots deferred to FP64 [n_queue]
   unsigned* band_bits;  // one bit per queue slot: set when the slot is a band ray
   int band_lanes;       // lanes of a band-pass warp that take rays (1..32)
+  // surrogate mode
+  const uint2* mlp_frag;       // fragment-ordered BF16 weights (bhs::NFRAG)
+  const float* mlp_bias;       // bhs::NBIAS
+  const unsigned char* surr_table;  // served (1) / fallback (0) per calibration bin
+  int surr_nb_lb, surr_nb_r;   // table dimensions: ln(b - b_c) bins x r_obs bins
+  int* surr_list;              // queue slots the surrogate hands back to the integrator
   TolR<float> tf;     // main pass, FP32 kernels
   TolR<double> td;    // main pass, FP64 mode
   TolR<double> tb;    // FP64 band pass of the MIXED mode

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mlp.cuh"
 #include "render.h"
 #include "tracer.cuh"
 
@@ -374,6 +375,38 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
 
 // Coherent pass: one 32-ray tile per warp grab, lanes in lock step, rays
 // over the step budget moved to the long-ray list.
+// The lanes of a warp integrate their rays in lock step until each has
+// ended (finished and stored) or used its step budget (moved to the
+// long-ray list).
+template <typename R, int MODE, typename OutR>
+__device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool active, long long q,
+                                               LocalStats& st) {
+  while (__any_sync(kFull, active)) {
+    if (active) {
+      Hit<R> hit;
+      if (advance<R, MODE>(p, r, hit, st)) {
+        finish_ray<R, OutR>(p, r, hit);
+        st.count_flag(hit.flags | r.aux);
+        active = false;
+      } else if (r.steps >= p.budget) {
+        const unsigned long long k = atomicAdd(&p.ws->long_count, 1ull);
+        Spill<R> sp;
+        sp.q = (int)q;
+        sp.steps = r.steps;
+        sp.aux = r.aux;
+        sp.pad = 0;
+        sp.u = r.u;
+        sp.v = r.v;
+        sp.phi = r.phi;
+        sp.h = r.h;
+        reinterpret_cast<Spill<R>*>(p.spill)[k] = sp;
+        st.c[ST_LONG]++;
+        active = false;
+      }
+    }
+  }
+}
+
 // Resident 256-thread blocks per SM the register allocation must allow:
 // 4 (64 registers) for the FP32 kernels, 2 for FP64.
 template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
@@ -397,30 +430,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
     Ray<R> r;
     R b;
     bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
-    while (__any_sync(kFull, active)) {
-      if (active) {
-        Hit<R> hit;
-        if (advance<R, MODE>(p, r, hit, st)) {
-          finish_ray<R, OutR>(p, r, hit);
-          st.count_flag(hit.flags | r.aux);
-          active = false;
-        } else if (r.steps >= p.budget) {
-          const unsigned long long k = atomicAdd(&p.ws->long_count, 1ull);
-          Spill<R> sp;
-          sp.q = (int)q;
-          sp.steps = r.steps;
-          sp.aux = r.aux;
-          sp.pad = 0;
-          sp.u = r.u;
-          sp.v = r.v;
-          sp.phi = r.phi;
-          sp.h = r.h;
-          reinterpret_cast<Spill<R>*>(p.spill)[k] = sp;
-          st.c[ST_LONG]++;
-          active = false;
-        }
-      }
-    }
+    integrate_warp<R, MODE, OutR>(p, r, active, q, st);
   }
   st.flush(p.ws);
 }
@@ -445,23 +455,31 @@ __device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ra
   return true;
 }
 
+// Sources of the list-driven pass.
+enum { SRC_SPILL = 0, SRC_BAND = 1, SRC_SURR = 2 };
+
 // Long-ray pass: every lane refills on its own from a list (saved long
-// rays, or FP64 band rays), warp-aggregated: one atomic per refill round.
-template <typename R, int MODE, typename OutR, bool FROM_SPILL>
+// rays, FP64 band rays, or rays the surrogate sends back to the integrator),
+// warp-aggregated: one atomic per refill round.
+template <typename R, int MODE, typename OutR, int SRC>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_longrays(const __grid_constant__ Params p) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned long long* next = FROM_SPILL ? &p.ws->long_next : &p.ws->band_next;
+  constexpr bool FROM_SPILL = SRC == SRC_SPILL;
+  unsigned long long* next = SRC == SRC_SPILL ? &p.ws->long_next
+                             : SRC == SRC_BAND ? &p.ws->band_next
+                                               : &p.ws->surr_next;
   const unsigned long long total =
-      FROM_SPILL ? *(volatile unsigned long long*)&p.ws->long_count
-                 : *(volatile unsigned long long*)&p.ws->band_count;
+      SRC == SRC_SPILL  ? *(volatile unsigned long long*)&p.ws->long_count
+      : SRC == SRC_BAND ? *(volatile unsigned long long*)&p.ws->band_count
+                        : *(volatile unsigned long long*)&p.ws->surr_count;
   LocalStats st;
   st.zero();
   Ray<R> r;
   bool active = false, exhausted = false;
   for (long long guard = 0; guard < (1ll << 40); ++guard) {
     if (!exhausted) {
-      const int lanes = FROM_SPILL ? 32 : p.band_lanes;
+      const int lanes = SRC == SRC_BAND ? p.band_lanes : 32;
       const unsigned need = __ballot_sync(kFull, !active && lane < lanes);
       if (need) {
         unsigned long long base = 0;
@@ -478,8 +496,8 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_longrays(const __grid_co
               const Spill<R> sp = reinterpret_cast<const Spill<R>*>(p.spill)[idx];
               active = restore_ray<R, MODE, OutR>(p, sp.q, &sp, r, st);
             } else {
-              active = restore_ray<R, MODE, OutR>(p, p.band_list[idx], nullptr, r, st);
-              if (active) st.c[ST_BAND] += 0;
+              const int* list = SRC == SRC_BAND ? p.band_list : p.surr_list;
+              active = restore_ray<R, MODE, OutR>(p, list[idx], nullptr, r, st);
             }
           }
         }
@@ -497,6 +515,109 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_longrays(const __grid_co
         active = false;
       }
     }
+  }
+  st.flush(p.ws);
+}
+
+// Surrogate pass.  One 32-ray tile per warp grab: set up each ray as the
+// MIXED coherent pass does (FP32 camera, orbital plane, impact parameter,
+// first disk-node angle psi0, periastron; band rays belong to the FP64 pass,
+// radial rays finish at once), decide whether the MLP may answer it --
+// no sphere cut by the orbital plane, inside the training domain, and a
+// calibration bin whose measured 99.9th-percentile error is within the
+// threshold -- run the MLP for the whole warp on the tensor cores and shade
+// the rays it answers: a served ray escapes at phi_inf = alpha + delta
+// unless the disk is met at psi0 or psi0 + pi first (u b from the MLP gives
+// the crossing radius).  The warp then integrates the rest in lock step with
+// the FP32 integrator, as the coherent pass would.
+// 128-thread blocks, three per SM: room stays for the FP64 band pass.
+__global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Params p) {
+  __shared__ uint2 s_frag[bhs::NFRAG];
+  __shared__ float s_bias[bhs::NBIAS];
+  __shared__ float s_feat[4][32 * bhs::K0];  // feature rows of each warp
+  for (int i = threadIdx.x; i < bhs::NFRAG; i += blockDim.x) s_frag[i] = p.mlp_frag[i];
+  for (int i = threadIdx.x; i < bhs::NBIAS; i += blockDim.x) s_bias[i] = p.mlp_bias[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  float* feat = s_feat[threadIdx.x >> 5];
+  const SceneR<float>& S = p.s.f;
+  const float M = S.M, iM = 1.0f / M;
+  const float bc_m = 5.19615242270663188f;  // 3 sqrt 3: b_crit / M
+  LocalStats st;
+  st.zero();
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ws->q_next, 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned long long)p.n_queue) break;
+    if (p.abort_after && base >= p.abort_after) {
+      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
+      break;
+    }
+    if (lane == 0) st.c[ST_GRABS]++;
+    const long long q = (long long)base + lane;
+    Ray<float> r;
+    float b = 0.0f;
+    bool active = (q < p.n_queue) && setup_slot<float, MODE_MIXED, float>(p, q, r, st, &b);
+    bool serve = false;
+    float r_obs = 0.0f;
+    float f[bhs::K0];
+    for (int k = 0; k < bhs::K0; ++k) f[k] = 0.0f;
+    if (active) {
+      r_obs = 1.0f / r.u;  // the set-up state is u = 1 / r_obs
+      const float bm = b * iM, rm = r_obs * iM;
+      bool ok = r.sph_mask == 0 && bm > bc_m + 1e-4f && rm >= 15.0f && rm <= 100.0f &&
+                (!p.s.disk_on || r.phi_node < 4.0f);
+      if (ok) {
+        bhs::surrogate_features<float>(bm, rm, p.s.disk_on ? r.phi_node : bhs::P_C, f);
+        const int ib = min(p.surr_nb_lb - 1, max(0, (int)((f[0] + 1.0f) * 0.5f * p.surr_nb_lb)));
+        const int ir = min(p.surr_nb_r - 1, max(0, (int)((rm - 15.0f) * (1.0f / 85.0f) * p.surr_nb_r)));
+        ok = p.surr_table[ib * p.surr_nb_r + ir] != 0;
+      }
+      serve = ok;
+    }
+    if (__any_sync(kFull, serve)) {
+      for (int k = 0; k < bhs::K0; ++k) feat[lane * bhs::K0 + k] = f[k];
+      __syncwarp();
+      float o[3];
+      bhs::mlp_warp(s_frag, s_bias, feat, o);
+      __syncwarp();
+      if (serve) {
+        const float delta = fmaf(o[0], bhs::D_S, bhs::D_C) * 4.0f * M / b;
+        const float alpha =
+            3.14159265358979f - asinf(fminf(1.0f, b * sqrtf(1.0f - 2.0f * M / r_obs) / r_obs));
+        const float phi_inf = alpha + delta;
+        Hit<float> hit;
+        hit.flags = BH_FLAG_ESC;
+        hit.phi = phi_inf;
+        hit.u = 0.0f;
+        hit.v = 0.0f;
+        if (p.s.disk_on) {
+          const float pa = r.phi_node, pb = pa + 3.14159265358979f;
+          const float ua = o[1] / b, ub = o[2] / b;
+          if (pa < phi_inf && ua > 0.0f && 1.0f / ua >= S.r_in && 1.0f / ua <= S.r_out) {
+            hit.flags = BH_FLAG_DISK;
+            hit.phi = pa;
+            hit.u = ua;
+          } else if (pb < phi_inf && ub > 0.0f && 1.0f / ub >= S.r_in && 1.0f / ub <= S.r_out) {
+            hit.flags = BH_FLAG_DISK;
+            hit.phi = pb;
+            hit.u = ub;
+          } else if (phi_inf > pa + 6.2831853f) {
+            serve = false;  // a third node crossing: beyond what the MLP predicts
+          }
+        }
+        if (serve) {
+          r.aux |= BH_FLAG_SURR;
+          finish_ray<float, float>(p, r, hit);
+          st.count_flag(hit.flags | r.aux);
+          st.c[ST_SURR]++;
+          active = false;
+        }
+      }
+    }
+    if (active) st.c[ST_FALLBACK]++;
+    integrate_warp<float, MODE_MIXED, float>(p, r, active, q, st);
   }
   st.flush(p.ws);
 }
@@ -539,7 +660,7 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     auto k1 = k_coherent<double, MODE_FP64, double>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
-    auto k2 = k_longrays<double, MODE_FP64, double, true>;
+    auto k2 = k_longrays<double, MODE_FP64, double, SRC_SPILL>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
@@ -547,7 +668,7 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     auto k1 = k_coherent<float, MODE_FP32, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
-    auto k2 = k_longrays<float, MODE_FP32, float, true>;
+    auto k2 = k_longrays<float, MODE_FP32, float, SRC_SPILL>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
@@ -555,12 +676,12 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
-    auto k2 = k_longrays<float, MODE_MIXED, float, true>;
+    auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     // FP64 band rays are few: one warp per block and one block per SM
     // sub-partition, so every warp gets an FP64 unit of its own
-    auto k3 = k_longrays<double, MODE_BAND64, float, false>;
+    auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
     k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
     rec(3);
   } else {
@@ -570,19 +691,51 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     cudaEventRecord(ls.fork, stream);
     cudaStreamWaitEvent(ls.side, ls.fork, 0);
     if (ls.band_ev && ls.band_ev[0]) record(ls.band_ev[0], ls.side);
-    auto k3 = k_longrays<double, MODE_BAND64, float, false>;
+    auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
     k3<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
     if (ls.band_ev && ls.band_ev[1]) record(ls.band_ev[1], ls.side);
     cudaEventRecord(ls.join, ls.side);
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
-    auto k2 = k_longrays<float, MODE_MIXED, float, true>;
+    auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     cudaStreamWaitEvent(stream, ls.join, 0);
     rec(3);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_t stream,
+                             cudaEvent_t* ev) {
+  cudaGetLastError();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(stream, &cap);
+  const bool capturing = cap == cudaStreamCaptureStatusActive;
+  auto record = [&](cudaEvent_t e, cudaStream_t s) {
+    if (!e) return;
+    if (capturing)
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s);
+  };
+  if (ev) record(ev[0], stream);
+  k_band_scan<<<ls.num_sms * 8, 256, 0, stream>>>(p);
+  cudaEventRecord(ls.fork, stream);
+  cudaStreamWaitEvent(ls.side, ls.fork, 0);
+  if (ls.band_ev) record(ls.band_ev[0], ls.side);
+  auto kb = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
+  kb<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
+  if (ls.band_ev) record(ls.band_ev[1], ls.side);
+  cudaEventRecord(ls.join, ls.side);
+  k_surrogate<<<ls.num_sms * 3, 128, 0, stream>>>(p);
+  if (ev) record(ev[1], stream);
+  auto kl = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
+  kl<<<ls.num_sms * occupancy(kl, ls.block), ls.block, 0, stream>>>(p);
+  if (ev) record(ev[2], stream);
+  cudaStreamWaitEvent(stream, ls.join, 0);
+  if (ev) record(ev[3], stream);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,13 @@ struct LaunchShape {
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
                           cudaEvent_t* ev);
 
+// Launch a surrogate render: band pre-pass, FP64 band pass on the side
+// stream, the surrogate pass (which integrates the rays it does not answer
+// itself), then the long-ray pass.  ev[0..3]: start, after the surrogate
+// pass, after the long-ray pass, end.
+cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_t stream,
+                             cudaEvent_t* ev);
+
 // Launch only the coherent pass (mode MODE_FP32 or MODE_FP64).  With
 // p.budget >= p.max_steps no ray is moved to the long-ray list, so the pass
 // finishes every ray itself and needs no spill or band storage.

@@ -364,7 +364,7 @@ __device__ __forceinline__ R next_sphere_window(const Ray<R>& r, R phi_from) {
 // 1 for a radial ray (handled by the caller with straight-line geometry).
 template <typename R>
 __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, Ray<R>& r,
-                           R* b_out, R* cos_a_out) {
+                           R* b_out, R* cos_a_out, R* sin_a_out = nullptr) {
   const R ir = R(1) / r_obs;
   r.e1x = P[0] * ir;
   r.e1y = P[1] * ir;
@@ -385,6 +385,7 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
   r.e2y = nz * r.e1x - nx * r.e1z;
   r.e2z = nx * r.e1y - ny * r.e1x;
   const R sin_a = d[0] * r.e2x + d[1] * r.e2y + d[2] * r.e2z;
+  if (sin_a_out) *sin_a_out = sin_a;
   const SceneR<R>& S = SR<R>(s);
   const R M = S.M;
   const R u0 = ir;
