@@ -92,6 +92,23 @@ def profile_traffic(form: str) -> float | None:
     return float(e["dram_bytes_per_launch"])
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (x itself for one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(rays_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job Mrays/s: each rank renders its own replica of the workload,
+    and the job takes as long as its slowest rank."""
+    return world * rays_per_rank * steps / seconds / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples while the timed region runs."""
 
@@ -310,13 +327,9 @@ def run_ours(args) -> None:
         barrier()
         t_wall = time.perf_counter() - t_wall
     bh.bh_scene_sync(sc.handle)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, "cuda")
     ms_per_step = ms / args.steps
-    value = world * n * args.steps / (ms * 1e-3) / 1e6
+    value = job_rate(n, args.steps, world, ms * 1e-3)
 
     # roofline: the FP32 integrator kernels (coherent + long-ray passes)
     int_ms = sum(km[0] + km[1] for km in kernel_ms)
@@ -355,14 +368,10 @@ def run_ours(args) -> None:
         for _ in range(args.steps):
             bh.bh_render_host(sc.handle, cams, wv, hv, hd, hf, hr, opts)
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         import ctypes
         from paper_2507_16165_gb300 import _capi
-        e2e = {"value": world * n * args.steps / dt / 1e6, "unit": UNIT,
+        e2e = {"value": job_rate(n, args.steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": len(cams) * (ctypes.sizeof(_capi.bh_camera) + 8),
                "d2h_bytes_per_step": n * (dirs.element_size() * 2 + 2 + 4)}
 

@@ -22,6 +22,10 @@ template <typename R>
 struct CamR {
   R pos[3], fwd[3], right[3], up[3];
   R sx, sy, r_obs;
+  R ir;              // 1 / r_obs
+  R px_scale;        // 2 sx / w: image-plane step per pixel column
+  R py_scale;        // 2 sy / h
+  R inv_tiles_x;     // 1 / tiles_x (a first guess for the tile row)
 };
 
 // Tolerances and caps in the kernel's arithmetic type.
@@ -165,6 +169,10 @@ inline void fill_cam_r(const CamK& c, CamR<R>* o) {
   o->sx = R(c.sx);
   o->sy = R(c.sy);
   o->r_obs = R(c.r_obs);
+  o->ir = R(1.0 / c.r_obs);
+  o->px_scale = R(2.0 * c.sx / c.w);
+  o->py_scale = R(2.0 * c.sy / c.h);
+  o->inv_tiles_x = R(1.0 / c.tiles_x);
 }
 
 }  // namespace bhk

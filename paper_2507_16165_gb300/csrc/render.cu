@@ -68,9 +68,21 @@ __device__ __forceinline__ bool slot_pixel(const Params& p, long long q, int* ca
   const CamK& c = p.cams[lo];
   const long long l = q - c.q_off;
   const int tile = (int)(l >> 5), i = (int)(l & 31);
-  const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
-  const int x = tx * p.tile_w + i % p.tile_w;
-  const int y = ty * p.tile_h + i / p.tile_w;
+  // tile row from an FP32 estimate, corrected to the exact quotient (the
+  // estimate is off by a few at most, for tile counts beyond 2^24)
+  int ty = (int)((float)tile * c.f.inv_tiles_x);
+  int tx = tile - ty * c.tiles_x;
+  while (tx < 0) {
+    --ty;
+    tx += c.tiles_x;
+  }
+  while (tx >= c.tiles_x) {
+    ++ty;
+    tx -= c.tiles_x;
+  }
+  // tile_w * tile_h = 32, so tile_w is a power of two
+  const int x = tx * p.tile_w + (i & (p.tile_w - 1));
+  const int y = ty * p.tile_h + (i >> (__ffs(p.tile_w) - 1));
   *cam = lo;
   *px = x;
   *py = y;
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Param
 // Newton on v(t) with dv/dt = h^2 accel(u), from the linear guess.
 template <typename R>
 __device__ __forceinline__ R turning_t(const Hermite<R>& H, R M3) {
-  const R va = H.d0, vb = H.d1;  // h-scaled derivatives at the ends
+  const R va = H.d_start(), vb = H.d_end();  // h-scaled derivatives at the ends
   R t = va / (va - vb);
   t = m_min(R(1), m_max(R(0), t));
   for (int it = 0; it < 4; ++it) {
@@ -251,9 +263,9 @@ __device__ __forceinline__ R turning_t(const Hermite<R>& H, R M3) {
 }
 
 
-template <typename R>
+template <typename R, typename E>
 __device__ __forceinline__ void consider(int type, R ph, unsigned id, int& bt, R& bp, unsigned& bid) {
-  const R tie = Num<R>::tie;
+  const R tie = R(Num<E>::tie);
   if (bt < 0 || ph < bp - tie ||
       (m_abs(ph - bp) <= tie && (type < bt || (type == bt && id < bid)))) {
     bt = type;
@@ -264,65 +276,88 @@ __device__ __forceinline__ void consider(int type, R ph, unsigned id, int& bt, R
 
 enum { EV_CAPT = 0, EV_SPHERE = 1, EV_DISK = 2, EV_ESC = 3 };
 
+// Arithmetic type of event location.  The FP64 band pass of the MIXED mode
+// steps in FP64 (the orbit's sensitivity near the photon sphere needs it)
+// but locates events in FP32: its results are stored in FP32 against a
+// 1e-4 rad budget, and FP32 root searches cost a small fraction of FP64 ones
+// on the narrow FP64 pipe.  Every other pass uses its stepping type.
+template <typename R, int MODE> struct EventT { using type = R; };
+template <> struct EventT<double, MODE_BAND64> { using type = float; };
+
 // Event handling for an accepted step [pa, pa + h] that may hold an event:
 // locate capture / escape roots, disk-node crossings and sphere entries on
 // the quintic Hermite interpolant and keep the earliest (ties within
-// Num<R>::tie: capture > sphere (lower index) > disk > escape).
+// Num<E>::tie: capture > sphere (lower index) > disk > escape).  With a
+// narrower event type E the interpolant's angles are taken relative to
+// shift = 2 pi floor(pa / 2 pi), so they stay small in FP32.
 template <typename R, int MODE>
 __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& pb, R h,
                             bool peri, Hit<R>& hit, LocalStats& st) {
+  using E = typename EventT<R, MODE>::type;
+  constexpr bool narrow = sizeof(E) < sizeof(R);
   const SceneK& s = p.s;
-  const SceneR<R>& S = SR<R>(s);
-  const R M3 = S.M3;
+  const SceneR<E>& S = SR<E>(s);
+  const E M3 = S.M3;
   const R pa = r.phi;
-  Hermite<R> H;
-  H.make(pa, h, r.u, r.v, r.f, un, vn, fn);
+  const R shift = narrow ? Num<R>::two_pi * m_floor(pa * R(0.15915494309189535)) : R(0);
+  const E pa_e = E(pa - shift);
+  Hermite<E> H;
+  H.make(pa_e, E(h), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
   if (MODE == MODE_MIXED && peri) {
     // periastron reset: truncate the step at the turning point and put the
     // state back on the orbit of the initial conditions, (u_p, 0) with u_p
     // from the FP64 cubic
-    const R tp = turning_t<R>(H, M3);
-    if (tp > R(0) && r.up == r.up) {
-      const R hp = tp * h;
+    const E tp = turning_t<E>(H, M3);
+    if (tp > E(0) && r.up == r.up) {
+      const R hp = R(tp) * h;
       pb = pa + hp;
       un = r.up;
       vn = R(0);
-      fn = accel(M3, un);
-      H.make(pa, hp, r.u, r.v, r.f, un, vn, fn);
+      fn = accel(SR<R>(s).M3, un);
+      H.make(pa_e, E(hp), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
     }
     r.aux |= kAuxPeriDone;
     st.c[ST_PERI]++;
   }
+  const R hs = R(H.h);  // length of the (possibly truncated) step
   int bt = -1;
   R bp = R(0);
   unsigned bid = 0;
-  if (un >= S.u_capt) consider<R>(EV_CAPT, pa + H.h * hermite_root<R>(H, S.u_capt, R(0), R(1)), 0u, bt, bp, bid);
-  if (un <= R(0)) consider<R>(EV_ESC, pa + H.h * hermite_root<R>(H, R(0), R(0), R(1)), 0u, bt, bp, bid);
+  // A disk or sphere hit in a step that ends captured lies before the
+  // capture radius is crossed (its radius is finite and outside it), and
+  // captured rays output no direction: capture is entered at the step's end
+  // without locating its root.
+  if (un >= SR<R>(s).u_capt) consider<R, E>(EV_CAPT, pb, 0u, bt, bp, bid);
+  if (un <= R(0))
+    consider<R, E>(EV_ESC, pa + hs * R(hermite_root<E>(H, E(0), E(0), E(1))), 0u, bt, bp, bid);
   for (int it = 0; it < 8 && r.phi_node <= pb; ++it) {
-    const R uk = H.u_at(r.phi_node);
-    if (uk > R(0)) {
-      const R rk = R(1) / uk;
+    const E uk = H.val_t(E((r.phi_node - pa) * R(H.ih)));
+    if (uk > E(0)) {
+      const E rk = E(1) / uk;
       if (rk >= S.r_in && rk <= S.r_out) {
-        consider<R>(EV_DISK, r.phi_node, 0u, bt, bp, bid);
+        consider<R, E>(EV_DISK, r.phi_node, 0u, bt, bp, bid);
         break;
       }
     }
     r.phi_node += Num<R>::pi;
   }
   if (pb >= r.phi_sph) {
+    const E pb_e = E(pb - shift);
     unsigned m = r.sph_mask;
     while (m) {
       const int k = __ffs(m) - 1;
       m &= m - 1;
-      R ph;
-      if (sphere_entry<R>(s, r, k, H, pa, pb, &ph)) consider<R>(EV_SPHERE, ph, (unsigned)k, bt, bp, bid);
+      E ph;
+      if (sphere_entry<E, R>(s, r, k, H, pa_e, pb_e, &ph))
+        consider<R, E>(EV_SPHERE, shift + R(ph), (unsigned)k, bt, bp, bid);
     }
     r.phi_sph = next_sphere_window<R>(r, pb);
   }
   if (bt < 0) return false;
+  const E tb = E((bp - pa) * R(H.ih));
   hit.phi = bp;
-  hit.u = H.u_at(bp);
-  hit.v = H.v_at(bp);
+  hit.u = R(H.val_t(tb));
+  hit.v = R(H.dval_t(tb) * H.ih);
   hit.flags = bt == EV_CAPT     ? BH_FLAG_CAPT
               : bt == EV_SPHERE ? (BH_FLAG_SPHERE | (bid << 8))
               : bt == EV_DISK   ? BH_FLAG_DISK
@@ -347,6 +382,9 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     st.c[ST_REJ]++;
     if (r.steps >= p.max_steps) {
       hit.flags = BH_FLAG_STEP_LIMIT;
+      hit.phi = r.phi;
+      hit.u = r.u;
+      hit.v = r.v;
       return true;
     }
     return false;
@@ -368,6 +406,9 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   r.phi = pb;
   if (r.steps >= p.max_steps || pb >= tol.phi_max) {
     hit.flags = BH_FLAG_STEP_LIMIT;
+    hit.phi = pb;
+    hit.u = un;
+    hit.v = vn;
     return true;
   }
   return false;

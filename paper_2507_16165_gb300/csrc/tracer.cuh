@@ -47,15 +47,29 @@ __device__ __forceinline__ void m_sincos_mapback(float x, float* s, float* c) {
   __sincosf(r, s, c);
 }
 __device__ __forceinline__ void m_sincos_mapback(double x, double* s, double* c) { sincos(x, s, c); }
+// sin and cos inside the FP32 event searches (sphere entry): the same
+// reduction and hardware approximation; a 4e-7 error in g moves a located
+// entry by far less than the FP32 passes' 1e-4 rad budget.  FP64 keeps the
+// accurate routine.
+__device__ __forceinline__ void m_sincos_evt(float x, float* s, float* c) { m_sincos_mapback(x, s, c); }
+__device__ __forceinline__ void m_sincos_evt(double x, double* s, double* c) { sincos(x, s, c); }
+// Quotient and reciprocal square root: the hardware approximations in FP32
+// (a few ulp, far inside the FP32 passes' error budget), correctly rounded
+// in FP64.
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
 __device__ __forceinline__ double m_ceil(double x) { return ceil(x); }
-__device__ __forceinline__ float m_rcp(float x) { return __frcp_rn(x); }
-// double reciprocal through single precision: only the error norm uses it,
-// where a relative error of 1e-7 in err^2 cannot change an accept decision
-// except within 1e-7 of the threshold
-__device__ __forceinline__ double m_rcp(double x) { return (double)__frcp_rn((float)x); }
+// Reciprocals of the error-norm scales only: the hardware approximation (a
+// few ulp), as a relative error of 1e-6 in err^2 cannot change an accept
+// decision except within 1e-6 of the threshold.  The double overload goes
+// through single precision for the same reason.
+__device__ __forceinline__ float m_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double m_rcp(double x) { return (double)__fdividef(1.0f, (float)x); }
 
 template <typename R> struct Num;
 template <> struct Num<float> {
@@ -202,49 +216,48 @@ __device__ R initial_step(R M3, R u, R v, R rtol, R atol, R cap) {
 }
 
 // ---------------------------------------------------------------------------
-// Quintic Hermite interpolant of u on [pa, pa + h] from u, h u', h^2 u''.
+// Quintic Hermite interpolant of u on [pa, pa + h] from u, h u', h^2 u''
+// at both ends, held in the power basis of the normalised t in [0, 1]:
+//   p(t) = c0 + c1 t + c2 t^2 + c3 t^3 + c4 t^4 + c5 t^5,
+// c0 = u_a, c1 = h v_a, c2 = h^2 f_a / 2, and with the end mismatches
+// A = u_b - (c0 + c1 + c2), B = h v_b - (c1 + 2 c2), C = h^2 f_b - 2 c2,
+// c3 = 10A - 4B + C/2, c4 = -15A + 7B - C, c5 = 6A - 3B + C/2 (the unique
+// solution of the three end conditions).  Values and slopes are then 5 and 4
+// fused multiply-adds.
 // ---------------------------------------------------------------------------
 template <typename R>
 struct Hermite {
   R pa, h, ih;
-  R u0, d0, s0, u1, d1, s1;
+  R c0, c1, c2, c3, c4, c5;
   __device__ __forceinline__ void make(R pa_, R h_, R ua, R va, R fa, R ub, R vb, R fb) {
     pa = pa_;
     h = h_;
-    ih = R(1) / h_;
-    u0 = ua;
-    d0 = h_ * va;
-    s0 = h_ * h_ * fa;
-    u1 = ub;
-    d1 = h_ * vb;
-    s1 = h_ * h_ * fb;
+    ih = m_div(R(1), h_);
+    const R hh = h_ * h_;
+    c0 = ua;
+    c1 = h_ * va;
+    c2 = R(0.5) * hh * fa;
+    const R A = ub - (c0 + c1 + c2);
+    const R B = m_fma(h_, vb, -m_fma(R(2), c2, c1));
+    const R C = m_fma(hh, fb, R(-2) * c2);
+    c3 = m_fma(R(10), A, m_fma(R(-4), B, R(0.5) * C));
+    c4 = m_fma(R(-15), A, m_fma(R(7), B, -C));
+    c5 = m_fma(R(6), A, m_fma(R(-3), B, R(0.5) * C));
   }
-  // value at normalised t in [0, 1]
+  // value at normalised t
   __device__ __forceinline__ R val_t(R t) const {
-    const R t2 = t * t, t3 = t2 * t;
-    // basis in Horner form in t for the t^3.. terms
-    const R h0 = R(1) + t3 * m_fma(t, m_fma(R(-6), t, R(15)), R(-10));
-    const R h1 = t + t3 * m_fma(t, m_fma(R(-3), t, R(8)), R(-6));
-    const R h2 = R(0.5) * t2 * (R(1) + t * m_fma(t, m_fma(R(-1), t, R(3)), R(-3)));
-    const R h3 = t3 * m_fma(t, m_fma(R(6), t, R(-15)), R(10));
-    const R h4 = t3 * m_fma(t, m_fma(R(-3), t, R(7)), R(-4));
-    const R h5 = R(0.5) * t3 * m_fma(t, t - R(2), R(1));
-    return u0 * h0 + d0 * h1 + s0 * h2 + u1 * h3 + d1 * h4 + s1 * h5;
+    return m_fma(t, m_fma(t, m_fma(t, m_fma(t, m_fma(t, c5, c4), c3), c2), c1), c0);
   }
   // d/dt of the interpolant
   __device__ __forceinline__ R dval_t(R t) const {
-    const R t2 = t * t;
-    const R g0 = t2 * m_fma(t, m_fma(R(-30), t, R(60)), R(-30));
-    const R g1 = R(1) + t2 * m_fma(t, m_fma(R(-15), t, R(32)), R(-18));
-    const R g2 = R(0.5) * t * (R(2) + t * m_fma(t, m_fma(R(-5), t, R(12)), R(-9)));
-    const R g3 = t2 * m_fma(t, m_fma(R(30), t, R(-60)), R(30));
-    const R g4 = t2 * m_fma(t, m_fma(R(-15), t, R(28)), R(-12));
-    const R g5 = R(0.5) * t2 * m_fma(t, m_fma(R(5), t, R(-8)), R(3));
-    return u0 * g0 + d0 * g1 + s0 * g2 + u1 * g3 + d1 * g4 + s1 * g5;
+    return m_fma(t, m_fma(t, m_fma(t, m_fma(t, R(5) * c5, R(4) * c4), R(3) * c3), R(2) * c2), c1);
   }
   __device__ __forceinline__ R t_of(R phi) const { return (phi - pa) * ih; }
   __device__ __forceinline__ R u_at(R phi) const { return val_t(t_of(phi)); }
   __device__ __forceinline__ R v_at(R phi) const { return dval_t(t_of(phi)) * ih; }
+  // end values in the scaled form: h u' at t = 0 and t = 1
+  __device__ __forceinline__ R d_start() const { return c1; }
+  __device__ __forceinline__ R d_end() const { return dval_t(R(1)); }
 };
 
 // Root t in [lo, hi] of val_t(t) - target, given a sign change, by Newton
@@ -252,7 +265,7 @@ struct Hermite {
 template <typename R>
 __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
   R flo = H.val_t(lo) - target;
-  R t = lo + (hi - lo) * (flo / (flo - (H.val_t(hi) - target)));
+  R t = lo + (hi - lo) * m_div(flo, flo - (H.val_t(hi) - target));
   if (!(t > lo && t < hi)) t = R(0.5) * (lo + hi);
   for (int it = 0; it < Num<R>::root_iters; ++it) {
     const R f = H.val_t(t) - target;
@@ -264,7 +277,7 @@ __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
       hi = t;
     }
     const R df = H.dval_t(t);
-    R tn = t - f / df;
+    R tn = t - m_div(f, df);
     if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
     if (m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7)) {
       t = tn;
@@ -307,15 +320,15 @@ struct Hit {
 template <typename R>
 __device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3], R d[3]) {
   const CamR<R>& C = CR<R>(c);
-  const R sx = (R(2) * (R(px) + R(0.5)) / R(c.w) - R(1)) * C.sx;
-  const R sy = (R(1) - R(2) * (R(py) + R(0.5)) / R(c.h)) * C.sy;
+  const R sx = m_fma(R(px) + R(0.5), C.px_scale, -C.sx);
+  const R sy = m_fma(-(R(py) + R(0.5)), C.py_scale, C.sy);
   R dd[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     P[k] = C.pos[k];
     dd[k] = C.fwd[k] + sx * C.right[k] + sy * C.up[k];
   }
-  const R inv = R(1) / m_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+  const R inv = m_rsqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = dd[k] * inv;
 }
@@ -365,21 +378,22 @@ __device__ __forceinline__ R next_sphere_window(const Ray<R>& r, R phi_from) {
 template <typename R>
 __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, Ray<R>& r,
                            R* b_out, R* cos_a_out, R* sin_a_out = nullptr) {
-  const R ir = R(1) / r_obs;
+  const R ir = m_div(R(1), r_obs);
   r.e1x = P[0] * ir;
   r.e1y = P[1] * ir;
   r.e1z = P[2] * ir;
   R cr0 = P[1] * d[2] - P[2] * d[1];
   R cr1 = P[2] * d[0] - P[0] * d[2];
   R cr2 = P[0] * d[1] - P[1] * d[0];
-  const R sn = m_sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+  const R sn2 = cr0 * cr0 + cr1 * cr1 + cr2 * cr2;
   const R cos_a = d[0] * r.e1x + d[1] * r.e1y + d[2] * r.e1z;
   *cos_a_out = cos_a;
-  if (sn < Num<R>::radial * r_obs) {
+  const R rad = Num<R>::radial * r_obs;
+  if (sn2 < rad * rad) {
     *b_out = R(0);
     return 1;
   }
-  const R isn = R(1) / sn;
+  const R isn = m_rsqrt(sn2);
   const R nx = cr0 * isn, ny = cr1 * isn, nz = cr2 * isn;
   r.e2x = ny * r.e1z - nz * r.e1y;
   r.e2y = nz * r.e1x - nx * r.e1z;
@@ -389,13 +403,13 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
   const SceneR<R>& S = SR<R>(s);
   const R M = S.M;
   const R u0 = ir;
-  const R cot = cos_a / sin_a;
+  const R cot = m_div(cos_a, sin_a);
   R b;
   if (s.ic == 0) {
-    b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * ir);
+    b = r_obs * sin_a * m_rsqrt(R(1) - R(2) * M * ir);
     r.v = -u0 * cot * m_sqrt(R(1) - R(2) * M * u0);
   } else {
-    b = r_obs * sin_a / m_sqrt(R(1) - R(2) * M * sin_a * sin_a * ir);
+    b = r_obs * sin_a * m_rsqrt(R(1) - R(2) * M * sin_a * sin_a * ir);
     r.v = -u0 * cot;
   }
   *b_out = b;
@@ -437,7 +451,7 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
 template <typename R>
 __device__ __forceinline__ R sphere_g(R cx, R cy, R K, R phi, R u) {
   R sp, cp;
-  m_sincos(phi, &sp, &cp);
+  m_sincos_evt(phi, &sp, &cp);
   return m_fma(K * u, u, m_fma(R(-2) * u, m_fma(cx, cp, cy * sp), R(1)));
 }
 
@@ -447,8 +461,13 @@ __device__ __forceinline__ R sphere_g(R cx, R cy, R K, R phi, R u) {
 // radius (the deviation w from the chord obeys w'' + w = 3Mu^2 with zero end
 // values; q = u_max / u_min on the step), so steps whose chord passes farther
 // than R' + that margin from the circle are rejected without a search.
-template <typename R>
-__device__ bool sphere_entry(const SceneK& s, const Ray<R>& r, int k, const Hermite<R>& H,
+//
+// The search runs in the event type R, which may be narrower than the ray's
+// stepping type T (the FP64 band pass of the MIXED mode locates its events
+// in FP32); pa, pb and the result are then angles relative to a multiple
+// of 2 pi, which leaves the sphere windows unchanged.
+template <typename R, typename T>
+__device__ bool sphere_entry(const SceneK& s, const Ray<T>& r, int k, const Hermite<R>& H,
                              R pa, R pb, R* phi_hit) {
   float wef;
   const float wsf = sphere_window(r, k, (float)pa, &wef);
@@ -457,25 +476,25 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<R>& r, int k, const Herm
   if (!(hi > lo)) return false;
   const SceneR<R>& S = SR<R>(s);
   const R c0 = S.c[k][0], c1 = S.c[k][1], c2 = S.c[k][2];
-  const R cx = c0 * r.e1x + c1 * r.e1y + c2 * r.e1z;
-  const R cy = c0 * r.e2x + c1 * r.e2y + c2 * r.e2z;
+  const R cx = c0 * R(r.e1x) + c1 * R(r.e1y) + c2 * R(r.e1z);
+  const R cy = c0 * R(r.e2x) + c1 * R(r.e2y) + c2 * R(r.e2z);
   const R K = S.K[k];
   const R rp2 = S.rad[k] * S.rad[k] - (S.c2[k] - (cx * cx + cy * cy));
   if (!(rp2 > R(0))) return false;
   const R ulo = H.u_at(lo), uhi = H.u_at(hi);
   if (ulo > R(0) && uhi > R(0)) {
     R sa, ca, sb, cb;
-    m_sincos(lo, &sa, &ca);
-    m_sincos(hi, &sb, &cb);
-    const R ia = R(1) / ulo, ib = R(1) / uhi;
+    m_sincos_evt(lo, &sa, &ca);
+    m_sincos_evt(hi, &sb, &cb);
+    const R ia = m_div(R(1), ulo), ib = m_div(R(1), uhi);
     const R ax = ca * ia, ay = sa * ia;
     const R bx = cb * ib - ax, by = sb * ib - ay;
     const R qx = cx - ax, qy = cy - ay;
     const R bb = m_fma(bx, bx, by * by);
-    R t = bb > R(0) ? m_fma(qx, bx, qy * by) / bb : R(0);
+    R t = bb > R(0) ? m_div(m_fma(qx, bx, qy * by), bb) : R(0);
     t = m_min(R(1), m_max(R(0), t));
     const R dx = qx - t * bx, dy = qy - t * by;
-    const R q = m_max(ulo, uhi) / m_min(ulo, uhi);
+    const R q = m_div(m_max(ulo, uhi), m_min(ulo, uhi));
     const R hh = hi - lo;
     const R margin = R(0.47) * S.M3 * q * q * hh * hh + R(1e-6);
     const R reach = m_sqrt(rp2) + margin;
@@ -559,8 +578,8 @@ __device__ __forceinline__ unsigned pack_rgba(float r, float g, float b) {
 
 template <typename R>
 __device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R phi) {
-  int i = (int)m_floor(R(16) * theta / Num<R>::pi);
-  int j = (int)m_floor(R(32) * phi / Num<R>::two_pi);
+  int i = (int)m_floor(theta * R(5.09295817894065074));   // 16 / pi
+  int j = (int)m_floor(phi * R(5.09295817894065074));     // 32 / (2 pi)
   i = min(15, max(0, i));
   j = min(31, max(0, j));
   const bool light = ((i + j) & 1) == 0;
