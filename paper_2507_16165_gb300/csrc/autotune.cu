@@ -24,8 +24,12 @@ TunedShape default_shape(int mode) {
   t.tile_w = 8;
   t.tile_h = 4;
   t.budget = (mode == BH_MODE_FP64) ? 256 : 48;
-  // MIXED: leave room on every SM for the band pass that runs alongside
-  if (mode == BH_MODE_MIXED) t.blocks_per_sm = 3;
+  // MIXED: 128-thread blocks, five per SM, leave registers on every SM for
+  // the FP64 band pass that runs alongside
+  if (mode == BH_MODE_MIXED) {
+    t.block = 128;
+    t.blocks_per_sm = 5;
+  }
   t.band_lanes = 32;
   t.band_warps = 4;
   return t;
@@ -58,19 +62,23 @@ extern "C" int bh_autotune(bh_scene* scene, const bh_camera* cams, int n_cams, c
   std::vector<TunedShape> cands;
   const int tiles[3][2] = {{8, 4}, {4, 8}, {16, 2}};
   const int budgets32[2] = {32, 64}, budgets64[2] = {128, 256};
-  for (int block : {128, 256})
+  // (block size, resident blocks per SM; 0 = as many as fit): MIXED keeps
+  // room for its concurrent band pass
+  const int res_mixed[3][2] = {{128, 5}, {128, 4}, {256, 2}};
+  const int res_other[2][2] = {{128, 0}, {256, 0}};
+  const bool mixed = mode == BH_MODE_MIXED;
+  const int n_res = mixed ? 3 : 2;
+  for (int ri = 0; ri < n_res; ++ri)
     for (auto& t : tiles)
-      for (int bi = 0; bi < 2; ++bi)
-        for (int bps : {0, 3}) {
-          if (bps == 3 && mode != BH_MODE_MIXED) continue;
-          TunedShape s = default_shape(mode);
-          s.block = block;
-          s.tile_w = t[0];
-          s.tile_h = t[1];
-          s.budget = mode == BH_MODE_FP64 ? budgets64[bi] : budgets32[bi];
-          s.blocks_per_sm = bps ? bps * 256 / block : 0;
-          cands.push_back(s);
-        }
+      for (int bi = 0; bi < 2; ++bi) {
+        TunedShape s = default_shape(mode);
+        s.block = mixed ? res_mixed[ri][0] : res_other[ri][0];
+        s.blocks_per_sm = mixed ? res_mixed[ri][1] : res_other[ri][1];
+        s.tile_w = t[0];
+        s.tile_h = t[1];
+        s.budget = mode == BH_MODE_FP64 ? budgets64[bi] : budgets32[bi];
+        cands.push_back(s);
+      }
   auto time_shape = [&](const TunedShape& s, float* best) -> int {
     bh_render_opts o = *opts;
     o.block_size = s.block;

@@ -65,7 +65,18 @@ struct CamK {
   long long q_off, out_off;
   CamR<float> f;
   CamR<double> d;
+  // u0^2 (1 - 2M u0) of the FP32 state u0 = f.ir and the FP32 mass: the
+  // u0 part of the first integral, for the MIXED periastron solve
+  double peri_k0;
+  float peri_k0f;
 };
+
+// Fill the periastron constant of a camera (after fill_cam_r).
+inline void fill_cam_peri(CamK& c, float M) {
+  const double u0 = (double)c.f.ir;
+  c.peri_k0 = u0 * u0 * (1.0 - 2.0 * (double)M * u0);
+  c.peri_k0f = (float)c.peri_k0;
+}
 
 enum StatId {
   ST_RAYS, ST_STEPS, ST_REJ, ST_ESC, ST_CAPT, ST_DISK, ST_SPH, ST_LIM, ST_BAND, ST_LONG,

@@ -262,6 +262,7 @@ int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
     c.out_off = o;
     fill_cam_r(c, &c.f);
     fill_cam_r(c, &c.d);
+    fill_cam_peri(c, sc->sk.f.M);
     q += 32LL * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }

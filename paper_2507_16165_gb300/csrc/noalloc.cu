@@ -156,6 +156,7 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     c.out_off = o;
     fill_cam_r(c, &c.f);
     fill_cam_r(c, &c.d);
+    fill_cam_peri(c, sk.f.M);
     q += 32LL * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }

@@ -141,16 +141,18 @@ __device__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a,
 
 // Periastron of the orbit through the FP32 initial state (u0, v0): the
 // middle root u_p of P(u) = 2M u^3 - u^2 + E0, E0 = v0^2 + u0^2 (1 - 2M u0).
-// FP32 start from the trigonometric form of the cubic's roots,
+// u0 = 1/r_obs is the same for every ray of a camera, so the camera table
+// holds k0 = u0^2 (1 - 2M u0) exactly in FP64 (and rounded to FP32); E0 is
+// then one FP64 fused multiply-add of the ray's v0.  FP32 start from the
+// trigonometric form of the cubic's roots,
 //   u_p = cos(acos(1 - 54 M^2 E0) / 3 - 2 pi / 3) / (3M) + 1/(6M),
-// one FP32 Newton step, then one Newton step with P evaluated in FP64 (the
-// slope only scales the step and stays in FP32).  NaN when there is no
-// turning point (b <= 3 sqrt(3) M).  Solved once per ray at set-up, where a
-// warp's lanes run it together.
-__device__ __forceinline__ float periastron64(float M, float u0f, float v0f) {
-  const double u0 = u0f, v0 = v0f, m2 = 2.0 * (double)M;
-  const double E0 = fma(v0, v0, u0 * u0 * fma(-m2, u0, 1.0));
-  const float E = (float)E0;
+// one FP32 Newton step, then one Newton step whose residual P(u) is
+// evaluated in FP64 (the slope only scales the small correction and stays
+// in FP32).  Seven operations on the FP64 pipe per ray.  NaN when there is
+// no turning point (b <= 3 sqrt(3) M).  Solved once per ray at set-up,
+// where a warp's lanes run it together.
+__device__ __forceinline__ float periastron64(float M, double m2, float v0f, double k0, float k0f) {
+  const float E = fmaf(v0f, v0f, k0f);
   if (!(M > 0.0f)) return sqrtf(E);
   const float x = fmaf(-54.0f * M * M, E, 1.0f);
   if (!(x > -1.0f)) return NAN;
@@ -158,9 +160,11 @@ __device__ __forceinline__ float periastron64(float M, float u0f, float v0f) {
   float u = fmaf(0.33333334f * im, cosf(acosf(x) * 0.33333334f - 2.0943951f), 0.16666667f * im);
   const float m2f = 2.0f * M;
   u -= fmaf(u * u, fmaf(m2f, u, -1.0f), E) / (u * fmaf(3.0f * m2f, u, -2.0f));
+  const double vd = v0f;
+  const double E0 = fma(vd, vd, k0);
   const double ud = u;
   const double f = fma(ud * ud, fma(m2, ud, -1.0), E0);
-  return (float)(ud - f * (double)(1.0f / (u * fmaf(3.0f * m2f, u, -2.0f))));
+  return fmaf(-(float)f, 1.0f / (u * fmaf(3.0f * m2f, u, -2.0f)), u);
 }
 
 // Set up the ray of queue slot q.  Returns true when the ray is to be
@@ -178,7 +182,7 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   r.aux = (MODE == MODE_FP64 || MODE == MODE_BAND64) ? BH_FLAG_FP64 : 0u;
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
-  if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, r, &b, &cos_a)) {
+  if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, CR<R>(c).ir, r, &b, &cos_a)) {
     radial_ray<R, OutR>(p, P, d, cos_a, out, r.aux, st);
     return false;
   }
@@ -192,7 +196,9 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
       return false;
     }
   }
-  if (MODE == MODE_MIXED) r.up = R(periastron64(p.s.f.M, float(r.u), float(r.v)));
+  if (MODE == MODE_MIXED)
+    r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
+  r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), tol.phi_max);
   r.steps = 0;
   const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
   // FP64 mirrors the oracle's starting step; FP32 starts at the step cap
@@ -353,6 +359,7 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
     }
     r.phi_sph = next_sphere_window<R>(r, pb);
   }
+  r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), TolPick<R, MODE>::get(p).phi_max);
   if (bt < 0) return false;
   const E tb = E((bp - pa) * R(H.ih));
   hit.phi = bp;
@@ -390,7 +397,10 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     return false;
   }
   R pb = r.phi + h;
-  bool slow = (un <= R(0)) | (un >= S.u_capt) | (pb >= r.phi_node) | (pb >= r.phi_sph);
+  // u <= 0 (escape) or u >= u_capt (capture) in one test: |u - c| >= c with
+  // c = u_capt / 2; node, sphere window and the phi cap through phi_evt
+  const R c = R(0.5) * S.u_capt;
+  bool slow = (m_abs(un - c) >= c) | (pb >= r.phi_evt);
   bool peri = false;
   if (MODE == MODE_MIXED) {
     peri = p.peri_reset && (r.v > R(0)) && (vn <= R(0)) && !(r.aux & kAuxPeriDone);
@@ -404,7 +414,7 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   r.v = vn;
   r.f = fn;
   r.phi = pb;
-  if (r.steps >= p.max_steps || pb >= tol.phi_max) {
+  if (r.steps >= p.max_steps || (slow && pb >= tol.phi_max)) {
     hit.flags = BH_FLAG_STEP_LIMIT;
     hit.phi = pb;
     hit.u = un;
@@ -449,8 +459,9 @@ __device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool 
 }
 
 // Resident 256-thread blocks per SM the register allocation must allow:
-// 4 (64 registers) for the FP32 kernels, 2 for FP64.
-template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
+// 3 (up to 80 registers, which the FP32 kernels need without spills) for
+// FP32, 2 for FP64.
+template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 3 : 2;
 
 template <typename R, int MODE, typename OutR>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
@@ -492,6 +503,7 @@ __device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ra
     r.f = accel(SR<R>(p.s).M3, r.u);
     for (int it = 0; it < 64 && r.phi_node <= r.phi; ++it) r.phi_node += Num<R>::pi;
     if (r.sph_mask) r.phi_sph = next_sphere_window<R>(r, r.phi);
+    r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), TolPick<R, MODE>::get(p).phi_max);
   }
   return true;
 }

@@ -179,17 +179,14 @@ __device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R
 // Computed in single precision for both arithmetic types: it only steers the
 // step size (a relative change of 1e-7 in h moves the solution by far less
 // than the tolerance); acceptance uses err2 <= 1 in the working precision.
+// Without branches: err2 = 0 gives log2 = -inf and a factor clamped to 10;
+// NaN propagates to fmaxf, which returns 0.2.  The 0.9 is folded into the
+// exponent as log2(0.9).
 template <typename R>
 __device__ __forceinline__ R step_factor(R err2) {
   const float e2 = (float)err2;
-  float fac;
-  if (!(e2 > 0.0f)) {
-    fac = (e2 == 0.0f) ? 10.0f : 0.2f;  // zero error grows, NaN shrinks
-  } else {
-    fac = 0.9f * exp2f(-0.1f * __log2f(e2));
-    fac = fminf(10.0f, fmaxf(0.2f, fac));
-  }
-  return R(fac);
+  const float fac = exp2f(fmaf(-0.1f, __log2f(e2), -0.15200309344504997f));
+  return R(fminf(10.0f, fmaxf(0.2f, fac)));
 }
 
 // Starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), capped at
@@ -297,6 +294,8 @@ struct Ray {
   R e1x, e1y, e1z, e2x, e2y, e2z;  // plane basis
   R phi_node;            // next disk node angle (> phi), or +inf
   R phi_sph;             // next sphere-window start, or +inf
+  R phi_evt;             // min(phi_node, phi_sph, phi_max): steps ending
+                         // before it need no event search
   R up;                  // periastron u of the orbit (MIXED reset), NaN if none
   unsigned sph_mask;     // spheres whose in-plane circle is non-empty
   float wc[kMaxSph];     // angular window of each such sphere: centre ...
@@ -376,9 +375,8 @@ __device__ __forceinline__ R next_sphere_window(const Ray<R>& r, R phi_from) {
 // Orbital-plane set-up of a camera ray.  Returns 0 for a ray to integrate,
 // 1 for a radial ray (handled by the caller with straight-line geometry).
 template <typename R>
-__device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, Ray<R>& r,
+__device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, R ir, Ray<R>& r,
                            R* b_out, R* cos_a_out, R* sin_a_out = nullptr) {
-  const R ir = m_div(R(1), r_obs);
   r.e1x = P[0] * ir;
   r.e1y = P[1] * ir;
   r.e1z = P[2] * ir;
