@@ -263,6 +263,10 @@ struct Hermite {
 
 // Root t in [lo, hi] of val_t(t) - target, given a sign change, by Newton
 // steps kept inside a shrinking bracket (bisection when Newton leaves it).
+// Convergence is tested on the Newton step before the bracket test: at the
+// root the sign of the residual is rounding noise, and a step that lands a
+// hair outside the bracket must end the search, not restart it from the
+// bracket's midpoint.
 template <typename R>
 __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
   R flo = H.val_t(lo) - target;
@@ -279,11 +283,8 @@ __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
     }
     const R df = H.dval_t(t);
     R tn = t - m_div(f, df);
+    if (m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7)) return m_min(hi, m_max(lo, tn));
     if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
-    if (m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7)) {
-      t = tn;
-      break;
-    }
     t = tn;
   }
   return t;
