@@ -24,11 +24,11 @@ TunedShape default_shape(int mode) {
   t.tile_w = 8;
   t.tile_h = 4;
   t.budget = (mode == BH_MODE_FP64) ? 256 : 48;
-  // MIXED: 128-thread blocks, five per SM, leave registers on every SM for
+  // MIXED: 128-thread blocks, six per SM, leave registers on every SM for
   // the FP64 band pass that runs alongside
   if (mode == BH_MODE_MIXED) {
     t.block = 128;
-    t.blocks_per_sm = 5;
+    t.blocks_per_sm = 6;
   }
   t.band_lanes = 32;
   t.band_warps = 4;
@@ -64,7 +64,7 @@ extern "C" int bh_autotune(bh_scene* scene, const bh_camera* cams, int n_cams, c
   const int budgets32[2] = {32, 64}, budgets64[2] = {128, 256};
   // (block size, resident blocks per SM; 0 = as many as fit): MIXED keeps
   // room for its concurrent band pass
-  const int res_mixed[3][2] = {{128, 5}, {128, 4}, {256, 2}};
+  const int res_mixed[3][2] = {{128, 6}, {128, 5}, {256, 3}};
   const int res_other[2][2] = {{128, 0}, {256, 0}};
   const bool mixed = mode == BH_MODE_MIXED;
   const int n_res = mixed ? 3 : 2;
