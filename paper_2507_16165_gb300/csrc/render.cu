@@ -153,13 +153,22 @@ __device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d
 // in FP32).  Seven operations on the FP64 pipe per ray.  NaN when there is
 // no turning point (b <= 3 sqrt(3) M).  Solved once per ray at set-up,
 // where a warp's lanes run it together.
+// arccos on [-1, 1] to 6.7e-5 rad (Abramowitz & Stegun 4.4.45); only the
+// starting guess of the periastron uses it, which two Newton steps refine.
+__device__ __forceinline__ float acos_guess(float x) {
+  const float a = fabsf(x);
+  const float p = fmaf(fmaf(fmaf(-0.0187293f, a, 0.0742610f), a, -0.2121144f), a, 1.5707288f);
+  const float r = sqrtf(fmaxf(0.0f, 1.0f - a)) * p;
+  return x >= 0.0f ? r : 3.14159265f - r;
+}
+
 __device__ __forceinline__ float periastron64(float M, double m2, float v0f, double k0, float k0f) {
   const float E = fmaf(v0f, v0f, k0f);
   if (!(M > 0.0f)) return sqrtf(E);
   const float x = fmaf(-54.0f * M * M, E, 1.0f);
   if (!(x > -1.0f)) return NAN;
   const float im = 1.0f / M;
-  float u = fmaf(0.33333334f * im, cosf(acosf(x) * 0.33333334f - 2.0943951f), 0.16666667f * im);
+  float u = fmaf(0.33333334f * im, __cosf(acos_guess(x) * 0.33333334f - 2.0943951f), 0.16666667f * im);
   const float m2f = 2.0f * M;
   u -= fmaf(u * u, fmaf(m2f, u, -1.0f), E) / (u * fmaf(3.0f * m2f, u, -2.0f));
   const double vd = v0f;
@@ -264,8 +273,10 @@ __device__ __forceinline__ R turning_t(const Hermite<R>& H, R M3) {
     const R g = H.dval_t(t);
     const R dg = H.h * H.h * accel(M3, H.val_t(t));
     if (dg == R(0)) break;
-    const R tn = t - g / dg;
-    t = m_min(R(1), m_max(R(0), tn));
+    const R tn = m_min(R(1), m_max(R(0), t - m_div(g, dg)));
+    const bool done = m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7);
+    t = tn;
+    if (done) break;
   }
   return t;
 }
