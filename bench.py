@@ -35,13 +35,18 @@ from paper_2507_16165_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Mrays/s at 4096^2 (FP64 / FP32 / MLP surrogate) at stated exit-dir error"
 UNIT = "Mrays/s"
-# FP32 FMA-pipe operations of one attempted Dormand-Prince step, counted from
-# dp5_attempt and step_factor in csrc/tracer.cuh: 26 MUL + 59 FMA in the
-# stages, error norm and scales, plus 4 in the step controller; an FMA counts
-# as two floating-point operations.
+# Algorithmic work of one attempted Dormand-Prince 5(4) step on (u, u') in
+# the tableau's first-order form: 26 MUL + 59 FMA in the stages, error
+# estimate, norm and scales, plus 4 in the step controller (89 FMA-pipe
+# operations; an FMA counts as two floating-point operations).  The kernels
+# take the same step in its second-order form with 57 operations, so the
+# achieved rate counts the work of the method, not of that rewrite.
 FLOP_PER_STEP = 2 * 59 + 26 + 4
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# FP64 fused multiply-adds per SM and cycle on GB300 (the peak ncu reports for
+# sm__sass_thread_inst_executed_op_dfma_pred_on: 2 per SM per cycle)
+FP64_LANES_PER_SM = 2
 STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9, "surrogate": 1e-3}
 # kernels one render launches: coherent + long-ray passes, and in MIXED the
 # band pre-pass and the FP64 band pass
@@ -331,15 +336,16 @@ def run_ours(args) -> None:
     ms_per_step = ms / args.steps
     value = job_rate(n, args.steps, world, ms * 1e-3)
 
-    # roofline: the FP32 integrator kernels (coherent + long-ray passes)
+    # roofline: the integrator kernels (coherent + long-ray passes) against
+    # the FP32 pipe, or the FP64 pipe in the FP64 form
     int_ms = sum(km[0] + km[1] for km in kernel_ms)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    if f64 or int_ms <= 0:
-        achieved = None
-    else:
-        achieved = steps32 * FLOP_PER_STEP / (int_ms * 1e-3) / 1e12
+    lanes = FP64_LANES_PER_SM if f64 else FP32_LANES_PER_SM
+    peak_tflops = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
+    n_steps = steps_all if f64 else steps32
+    achieved = n_steps * FLOP_PER_STEP / (int_ms * 1e-3) / 1e12 if int_ms > 0 else None
+    prec = "FP64" if f64 else "FP32"
     roofline = {
         "bound": "alu",
         "achieved": achieved,
@@ -347,11 +353,11 @@ def run_ours(args) -> None:
         "unit": "TFLOP/s",
         "frac": (achieved / peak_tflops) if achieved is not None else None,
         "traffic": profile_traffic(args.form),
-        "kernel": "k_coherent + k_longrays (FP32 Dormand-Prince steps)",
-        "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+        "kernel": f"k_coherent + k_longrays ({prec} Dormand-Prince steps)",
+        "peak_source": f"derived: {SM_COUNT} SMs x {lanes} {prec} FMA lanes x 2 FLOP x "
                        f"{sm_max:.0f} MHz (max SM clock)",
-        "algorithmic": f"{FLOP_PER_STEP} FLOP per attempted FP32 step x "
-                       f"{steps32 / args.steps:.0f} steps per frame",
+        "algorithmic": f"{FLOP_PER_STEP} FLOP per attempted {prec} step x "
+                       f"{n_steps / args.steps:.0f} steps per frame",
         "integrator_ms_per_step": int_ms / args.steps,
     }
 
