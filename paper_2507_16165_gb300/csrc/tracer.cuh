@@ -53,12 +53,38 @@ __device__ __forceinline__ void m_sincos_mapback(double x, double* s, double* c)
 // accurate routine.
 __device__ __forceinline__ void m_sincos_evt(float x, float* s, float* c) { m_sincos_mapback(x, s, c); }
 __device__ __forceinline__ void m_sincos_evt(double x, double* s, double* c) { sincos(x, s, c); }
+// Single special-function-unit instructions (PTX approximate forms with
+// denormals flushed to zero): reciprocal, reciprocal square root, base-2
+// logarithm and exponential, each within a few ulp.  Their operands here are
+// normal numbers or the limits 0 and infinity, whose results (infinity,
+// -infinity, 0) the callers handle.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Quotient and reciprocal square root: the hardware approximations in FP32
 // (a few ulp, far inside the FP32 passes' error budget), correctly rounded
 // in FP64.
-__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float m_div(float a, float b) { return a * rcp_approx(b); }
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
-__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrt_approx(x); }
 __device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
@@ -68,8 +94,8 @@ __device__ __forceinline__ double m_ceil(double x) { return ceil(x); }
 // few ulp), as a relative error of 1e-6 in err^2 cannot change an accept
 // decision except within 1e-6 of the threshold.  The double overload goes
 // through single precision for the same reason.
-__device__ __forceinline__ float m_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double m_rcp(double x) { return (double)__fdividef(1.0f, (float)x); }
+__device__ __forceinline__ float m_rcp(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double m_rcp(double x) { return (double)rcp_approx((float)x); }
 
 template <typename R> struct Num;
 template <> struct Num<float> {
@@ -189,7 +215,7 @@ __device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R
 template <typename R>
 __device__ __forceinline__ R step_factor(R err2) {
   const float e2 = (float)err2;
-  const float fac = exp2f(fmaf(-0.1f, __log2f(e2), -0.15200309344504997f));
+  const float fac = ex2_approx(fmaf(-0.1f, lg2_approx(e2), -0.15200309344504997f));
   return R(fminf(10.0f, fmaxf(0.2f, fac)));
 }
 
