@@ -31,11 +31,8 @@ __device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(
 __device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
-__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
-__device__ __forceinline__ float m_acos(float x) { return acosf(x); }
 __device__ __forceinline__ double m_acos(double x) { return acos(x); }
-__device__ __forceinline__ float m_asin(float x) { return asinf(x); }
 __device__ __forceinline__ double m_asin(double x) { return asin(x); }
 // sin and cos for the map-back: Cody & Waite argument reduction by 2 pi with
 // a two-term split of 2 pi (float(2 pi) and its residual), then the hardware
@@ -86,6 +83,46 @@ __device__ __forceinline__ float m_div(float a, float b) { return a * rcp_approx
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_rsqrt(float x) { return rsqrt_approx(x); }
 __device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Inverse trigonometric functions for the FP32 paths from the polynomial
+// approximations of Abramowitz & Stegun: 4.4.49 for arctan on [-1, 1]
+// (error below 2e-8) and 4.4.46 for arccos on [0, 1] (below 2e-8), with
+// octant and sign reduction; FP32 evaluation adds about 1e-7.  The FP64
+// overloads are the accurate library routines.
+__device__ __forceinline__ float atan_unit(float t) {  // arctan, |t| <= 1
+  const float t2 = t * t;
+  float p = fmaf(t2, 0.0028662257f, -0.0161657367f);
+  p = fmaf(t2, p, 0.0429096138f);
+  p = fmaf(t2, p, -0.0752896400f);
+  p = fmaf(t2, p, 0.1065626393f);
+  p = fmaf(t2, p, -0.1420889944f);
+  p = fmaf(t2, p, 0.1999355085f);
+  p = fmaf(t2, p, -0.3333314528f);
+  return fmaf(t * t2, p, t);
+}
+__device__ __forceinline__ float m_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  float a = mx > 0.0f ? atan_unit(mn * rcp_approx(mx)) : 0.0f;
+  if (ay > ax) a = 1.57079632679489662f - a;
+  if (x < 0.0f) a = 3.14159265358979324f - a;
+  return copysignf(a, y);
+}
+__device__ __forceinline__ float m_acos(float x) {
+  const float a = fminf(1.0f, fabsf(x));
+  float p = fmaf(a, -0.0012624911f, 0.0066700901f);
+  p = fmaf(a, p, -0.0170881256f);
+  p = fmaf(a, p, 0.0308918810f);
+  p = fmaf(a, p, -0.0501743046f);
+  p = fmaf(a, p, 0.0889789874f);
+  p = fmaf(a, p, -0.2145988016f);
+  p = fmaf(a, p, 1.5707963050f);
+  const float r = sqrtf(1.0f - a) * p;
+  return x < 0.0f ? 3.14159265358979324f - r : r;
+}
+__device__ __forceinline__ float m_asin(float x) {
+  return 1.57079632679489662f - m_acos(x);
+}
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
@@ -374,10 +411,10 @@ __device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, 
   const float cy = c0 * (float)r.e2x + c1 * (float)r.e2y + c2 * (float)r.e2z;
   const float rho2 = cx * cx + cy * cy;
   const float rp2 = fmaxf(0.0f, s.f.rad[k] * s.f.rad[k] - (s.f.c2[k] - rho2));
-  float pc = atan2f(cy, cx);
+  float pc = m_atan2(cy, cx);
   if (pc < 0.0f) pc += 6.28318530717958647692f;
   r.wc[k] = pc;
-  r.wd[k] = asinf(fminf(1.0f, sqrtf(rp2 / rho2))) + 1e-4f;
+  r.wd[k] = m_asin(fminf(1.0f, sqrtf(rp2 * rcp_approx(rho2)))) + 1e-4f;
 }
 
 // The first window of sphere k whose end lies at or after phi_from:
@@ -676,7 +713,7 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) 
     rgba = sky_rgba<T>(s.seed, th, ph);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
-    const float t = exp2f(0.75f * __log2f(s.f.r_in / rr));
+    const float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
     const float k = fmaf(0.7f, t, 0.3f);
     rgba = pack_rgba(k, fmaf(0.65f, t, 0.35f) * k, fmaf(0.9f * t, t, 0.1f) * k);
   } else {  // sphere
