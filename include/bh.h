@@ -139,6 +139,9 @@ typedef struct bh_render_opts {
                            -1 = off                                         */
   uint32_t abort_after; /* fault injection: stop after this many work items
                            and report BH_E_DEVICE (0 = off)                 */
+  double h_max_far;   /* largest step in rad for rays with |b - 3 sqrt(3) M|
+                         >= 2M in the FP32 passes, whose outputs are far less
+                         sensitive to stepping errors (0: 0.4; FP64: h_max) */
 } bh_render_opts;
 
 typedef struct bh_stats {

@@ -55,7 +55,8 @@ class bh_render_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p),
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
-                ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32)]
+                ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
+                ("h_max_far", ctypes.c_double)]
 
 
 class bh_stats(ctypes.Structure):

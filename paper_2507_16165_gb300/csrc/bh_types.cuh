@@ -32,7 +32,12 @@ struct CamR {
 template <typename R>
 struct TolR {
   R rtol, atol, phi_max, h_max, band;
+  R h_far;  // step cap of rays with |b - b_c| >= kFarB (FP32 passes)
 };
+
+// Rays at least this far from the critical impact parameter (units of M)
+// take the relaxed step cap h_far in the FP32 passes.
+constexpr double kFarB = 2.0;
 
 // Scene constants, passed by value in every kernel's parameter block.
 struct SceneK {
@@ -124,6 +129,7 @@ struct Params {
   double band;                  // |b - b_c| below which MIXED defers to FP64
   double phi_max;
   double h_max;                 // step-size cap of the main pass (FP64 band: none)
+  double h_max_far;             // FP32 step cap of rays with |b - b_c| >= kFarB
   int max_steps;
   int peri_reset;
   unsigned long long abort_after;  // stop grabbing work past this slot (0 = off)

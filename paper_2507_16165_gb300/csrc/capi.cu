@@ -232,7 +232,7 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
       opts->block_size != 256)
     return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
-      opts->phi_max < 0 || opts->h_max < 0 ||
+      opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
   return BH_OK;
@@ -283,6 +283,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.band_rtol = o->band_rtol > 0 ? o->band_rtol : 1e-9;
   c.phi_max = o->phi_max > 0 ? o->phi_max : 64.0;
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
+  c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
   const TunedShape t = tuned_shape(sc, o->mode);
   c.block = o->block_size ? o->block_size : t.block;
@@ -385,6 +386,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.band = cfg.band;
   p.phi_max = cfg.phi_max;
   p.h_max = cfg.h_max;
+  p.h_max_far = cfg.h_max_far;
   p.max_steps = cfg.max_steps;
   p.peri_reset = cfg.peri_reset;
   p.abort_after = cfg.abort_after;
@@ -399,9 +401,10 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
 }
 
 void fill_tolerances(Params& p) {
-  p.tf = TolR<float>{(float)p.rtol, (float)p.atol, (float)p.phi_max, (float)p.h_max, (float)p.band};
-  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band};
-  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band};
+  p.tf = TolR<float>{(float)p.rtol, (float)p.atol, (float)p.phi_max, (float)p.h_max, (float)p.band,
+                     (float)p.h_max_far};
+  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band, p.h_max_far};
+  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band, INFINITY};
 }
 
 extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cams, const int* w,

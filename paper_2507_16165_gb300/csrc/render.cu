@@ -215,6 +215,9 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   // FP64 mirrors the oracle's starting step; FP32 starts at the step cap
   // (the controller shrinks it when the first attempt is rejected)
   r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01)) : tol.h_max;
+  // FP32 rays far from the photon sphere may take longer steps (their exit
+  // directions amplify stepping errors far less); they still start at h_max
+  if (!d64 && m_abs(b - SR<R>(p.s).b_crit) >= R(kFarB) * SR<R>(p.s).M) r.aux |= kAuxFar;
   return true;
 }
 
@@ -397,7 +400,7 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   if (sizeof(R) == 8) st.c[ST_STEPS64]++;
   const R h = r.h;
   r.h = h * step_factor<R>(err2);
-  r.h = m_min(r.h, tol.h_max);
+  r.h = m_min(r.h, (r.aux & kAuxFar) ? tol.h_far : tol.h_max);
   if (!(err2 <= R(1))) {
     st.c[ST_REJ]++;
     if (r.steps >= p.max_steps) {

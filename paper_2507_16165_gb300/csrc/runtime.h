@@ -48,7 +48,7 @@ struct bh_scene {
 // Resolved options of one render.
 struct RenderConfig {
   int mode;
-  double rtol, atol, band, band_rtol, phi_max, h_max;
+  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far;
   int max_steps;
   int block, blocks_per_sm, tile_w, tile_h, budget;
   int band_lanes, band_warps;

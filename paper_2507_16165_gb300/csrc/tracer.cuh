@@ -374,6 +374,7 @@ struct Ray {
 };
 
 constexpr unsigned kAuxPeriDone = 1u << 16;
+constexpr unsigned kAuxFar = 1u << 17;  // ray takes the relaxed step cap h_far
 
 // Event produced when a ray terminates.
 template <typename R>
