@@ -47,10 +47,16 @@ FP32_LANES_PER_SM = 128
 # FP64 fused multiply-adds per SM and cycle on GB300 (the peak ncu reports for
 # sm__sass_thread_inst_executed_op_dfma_pred_on: 2 per SM per cycle)
 FP64_LANES_PER_SM = 2
-STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9, "surrogate": 1e-3}
+# Algorithmic work of one classical Runge-Kutta step of the paper's own
+# stepping mode: 4 right-hand sides (FMA + MUL), 6 stage arguments (FMA),
+# the two weighted sums (2 x (3 ADD + MUL + FMA)) and h/6: 37 FLOP.
+FLOP_PER_RK4_STEP = 4 * 3 + 6 * 2 + 2 * 6 + 1
+STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9, "surrogate": 1e-3,
+                "paper": 1e-4, "paper_fp32": 1e-4}
 # kernels one render launches: coherent + long-ray passes, and in MIXED the
 # band pre-pass and the FP64 band pass
-KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2, "surrogate": 4}
+KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2, "surrogate": 4, "paper": 1,
+                      "paper_fp32": 1}
 
 
 def workload(form: str, size: int, name: str = "c3"):
@@ -62,6 +68,10 @@ def workload(form: str, size: int, name: str = "c3"):
         return replace(W.config5(64), mode=form)
     if form == "surrogate":
         return W.config4(size)
+    if form in ("paper", "paper_fp32"):
+        # the paper's own fixed-step polyline on the config-3 scene
+        from dataclasses import replace
+        return replace(W.config3(size, "fp64"), mode=form, name=f"c3_{form}_{size}")
     return W.config3(size, form)
 
 
@@ -276,12 +286,14 @@ def run_ours(args) -> None:
     wv = [c.w for c in w.cameras]
     hv = [c.h for c in w.cameras]
     stream = torch.cuda.Stream()
-    f64 = args.form == "fp64"
+    f64 = args.form in ("fp64", "paper")
+    paper = args.form in ("paper", "paper_fp32")
     dirs = torch.empty(2 * n, dtype=torch.float64 if f64 else torch.float32, device="cuda")
     flags = torch.empty(n, dtype=torch.int16, device="cuda")
     rgba = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-    opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band)
+    opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band,
+                          paper_eps=args.paper_eps)
 
     surrogate = None
     if args.form == "surrogate":
@@ -344,8 +356,10 @@ def run_ours(args) -> None:
     lanes = FP64_LANES_PER_SM if f64 else FP32_LANES_PER_SM
     peak_tflops = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
     n_steps = steps_all if f64 else steps32
-    achieved = n_steps * FLOP_PER_STEP / (int_ms * 1e-3) / 1e12 if int_ms > 0 else None
+    flop_step = FLOP_PER_RK4_STEP if paper else FLOP_PER_STEP
+    achieved = n_steps * flop_step / (int_ms * 1e-3) / 1e12 if int_ms > 0 else None
     prec = "FP64" if f64 else "FP32"
+    method = f"fixed-step Runge-Kutta 4, eps {args.paper_eps}" if paper else "Dormand-Prince"
     roofline = {
         "bound": "alu",
         "achieved": achieved,
@@ -353,10 +367,10 @@ def run_ours(args) -> None:
         "unit": "TFLOP/s",
         "frac": (achieved / peak_tflops) if achieved is not None else None,
         "traffic": profile_traffic(args.form),
-        "kernel": f"k_coherent + k_longrays ({prec} Dormand-Prince steps)",
+        "kernel": ("k_paper" if paper else "k_coherent + k_longrays") + f" ({prec} {method} steps)",
         "peak_source": f"derived: {SM_COUNT} SMs x {lanes} {prec} FMA lanes x 2 FLOP x "
                        f"{sm_max:.0f} MHz (max SM clock)",
-        "algorithmic": f"{FLOP_PER_STEP} FLOP per attempted {prec} step x "
+        "algorithmic": f"{flop_step} FLOP per attempted {prec} step x "
                        f"{n_steps / args.steps:.0f} steps per frame",
         "integrator_ms_per_step": int_ms / args.steps,
     }
@@ -394,7 +408,7 @@ def run_ours(args) -> None:
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else ("f32" if paper else "f32+f64"),
         "data": "synthetic",
         "config": {"workload": w.name, "form": args.form, "rays_per_step": n,
                    "size": (f"{args.size}x{args.size}" if args.workload == "c3"
@@ -404,6 +418,7 @@ def run_ours(args) -> None:
                    "disk": list(w.scene.disk), "spheres": len(w.scene.spheres),
                    "rtol": w.rtol, "atol": w.atol,
                    "band": w.band, "stated_exit_dir_error_rad": STATED_ERROR[args.form],
+                   "paper_eps": args.paper_eps if paper else None,
                    "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps (outside the events)",
                    "launch": ("autotuned shape, one CUDA-graph replay per step: " + json.dumps(tuned))
@@ -438,7 +453,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate"), default="mixed")
+    ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate", "paper", "paper_fp32"),
+                    default="mixed")
+    ap.add_argument("--paper-eps", type=float, default=0.01,
+                    help="fixed step of the paper's own stepping forms (rad)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--workload", choices=("c3", "c5"), default="c3")
     ap.add_argument("--no-e2e", action="store_true")

@@ -68,6 +68,13 @@ extern "C" {
 #define BH_MODE_MIXED 2     /* FP32 stepping; FP64 for the periastron reset
                                and for rays with |b - 3 sqrt(3) M| < band   */
 #define BH_MODE_SURROGATE 3 /* MLP surrogate with integrator fallback       */
+#define BH_MODE_PAPER_EPS 4 /* the paper's own stepping (Sec. 2.1-2.2): fixed
+                               steps paper_eps in phi with the classical
+                               fourth-order Runge-Kutta method, straight
+                               segments between the points, objects found by
+                               segment intersection; FP64 (the paper's
+                               precision), directions stored as double     */
+#define BH_MODE_PAPER_EPS_FP32 5 /* the same in FP32, directions as float  */
 
 /* ---- initial-condition conventions (Sec. 2.2 reading) ---------------- */
 #define BH_IC_STATIC 0    /* camera is a static observer (default)        */
@@ -142,6 +149,8 @@ typedef struct bh_render_opts {
   double h_max_far;   /* largest step in rad for rays with |b - 3 sqrt(3) M|
                          >= 2M in the FP32 passes, whose outputs are far less
                          sensitive to stepping errors (0: 0.4; FP64: h_max) */
+  double paper_eps;   /* fixed step in rad of the BH_MODE_PAPER_EPS modes
+                         (0: 0.01)                                          */
 } bh_render_opts;
 
 typedef struct bh_stats {

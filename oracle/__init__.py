@@ -60,7 +60,11 @@ class _Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("phi_max", ctypes.c_double), ("max_steps", ctypes.c_long),
                 ("eps_r", ctypes.c_double), ("eps_ang", ctypes.c_double),
-                ("eps_b", ctypes.c_double)]
+                ("eps_b", ctypes.c_double), ("method", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
+METHOD_DP5 = 0
+METHOD_POLYLINE = 1
 
 
 _lock = threading.Lock()
@@ -142,9 +146,10 @@ def _cams(cams) -> ctypes.Array:
 
 
 def opts(rtol=1e-10, atol=1e-10, phi_max=64.0, max_steps=100000,
-         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6) -> _Opts:
-    """Integration tolerances, caps and ambiguity thresholds."""
-    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b)
+         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6, method=METHOD_DP5, eps=0.01) -> _Opts:
+    """Integration tolerances, caps and ambiguity thresholds; method 1 is the
+    paper's fixed-step polyline with step eps (Sec. 2.1-2.2)."""
+    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b, method, eps)
 
 
 def _ptr(a: np.ndarray) -> int:

@@ -21,6 +21,9 @@
  *     Wanner error norm and step controller; the paper's piecewise-linear
  *     segments (Sec. 2.1) are replaced by exact event location on the
  *     quintic Hermite interpolant of each accepted step;
+ *   - the paper's own fixed-step polyline is kept as method 1 (classical
+ *     Runge-Kutta at a fixed step eps, segment intersection), to measure
+ *     that approach against the adaptive one;
  *   - events: escape (u -> 0), capture (u >= 1/(2M)), thin equatorial disk
  *     annulus, opaque spheres; the result is mapped back to 3-D and shaded
  *     against a procedural checkerboard sky.
@@ -79,6 +82,9 @@ typedef struct {
   double phi_max;
   long max_steps;
   double eps_r, eps_ang, eps_b; /* ambiguity thresholds */
+  int method;  /* 0: Dormand-Prince 5(4) with exact events; 1: the paper's
+                  fixed-step polyline (Sec. 2.1-2.2) */
+  double eps;  /* step in phi of method 1 */
 } or_opts;
 
 typedef struct {
@@ -624,6 +630,171 @@ static void dir_angles(const double d[3], double *theta, double *phi) {
 /* ------------------------------------------------------------------ */
 /* One pixel: the whole path                                            */
 /* ------------------------------------------------------------------ */
+/* Thin-disk temperature ramp at radius r: t = (r_in / r)^(3/4). */
+static void disk_rgb(const or_scene *sc, double r, double rgb[3]) {
+  double t = pow(sc->disk_r_in / r, 0.75);
+  double k = 0.3 + 0.7 * t;
+  rgb[0] = 1.0 * k;
+  rgb[1] = (0.35 + 0.65 * t) * k;
+  rgb[2] = (0.1 + 0.9 * t * t) * k;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's own stepping (Sec. 2.1-2.2, Fig. 1): points of the ray at   */
+/* fixed steps eps in phi, computed with the classical fourth-order        */
+/* Runge-Kutta method, joined by straight segments in 3-D; objects are     */
+/* found by intersecting each segment with them.  Readings: the point      */
+/* beyond which u <= 0 ends the ray, escaping along the angle where the    */
+/* straight line between the last two (phi, u) values reaches u = 0; a     */
+/* segment whose end has u >= 1/(2M) and that meets no object is captured. */
+/* ------------------------------------------------------------------ */
+static void rk4_step(double M, double h, double *u, double *v) {
+  double u0 = *u, v0 = *v;
+  double ku1 = v0, kv1 = accel(M, u0);
+  double ku2 = v0 + 0.5 * h * kv1, kv2 = accel(M, u0 + 0.5 * h * ku1);
+  double ku3 = v0 + 0.5 * h * kv2, kv3 = accel(M, u0 + 0.5 * h * ku2);
+  double ku4 = v0 + h * kv3, kv4 = accel(M, u0 + h * ku3);
+  *u = u0 + h / 6.0 * (ku1 + 2.0 * ku2 + 2.0 * ku3 + ku4);
+  *v = v0 + h / 6.0 * (kv1 + 2.0 * kv2 + 2.0 * kv3 + kv4);
+}
+
+/* 3-D point of the orbit at plane angle phi and u = 1/r */
+static void plane_point(const or_plane *pl, double phi, double u, double x[3]) {
+  double c = cos(phi), s = sin(phi);
+  for (int k = 0; k < 3; ++k) x[k] = (c * pl->e1[k] + s * pl->e2[k]) / u;
+}
+
+typedef struct {
+  unsigned flags, sphere_id, ambig;
+  double phi_esc;   /* escape angle */
+  double x[3];      /* hit position */
+  double t[3];      /* unit direction of the segment that hit */
+  long steps;
+} or_poly_event;
+
+static void trace_polyline(const or_scene *sc, const or_opts *o, const or_plane *pl,
+                           or_poly_event *ev) {
+  double M = sc->mass, eps = o->eps;
+  double u = pl->u0, v = pl->v0, phi = 0.0;
+  double u_capt = (M > 0) ? 1.0 / (2.0 * M) : INFINITY;
+  double xa[3];
+  plane_point(pl, 0.0, u, xa);
+  ev->ambig = 0;
+  ev->sphere_id = 0;
+  for (long steps = 0;; ++steps) {
+    ev->steps = steps;
+    if (steps >= o->max_steps || phi >= o->phi_max) {
+      ev->flags = OR_STEP_LIMIT;
+      return;
+    }
+    double un = u, vn = v;
+    rk4_step(M, eps, &un, &vn);
+    double pb = phi + eps;
+    if (un <= 0.0) {
+      ev->flags = OR_ESC;
+      ev->phi_esc = phi + eps * u / (u - un);
+      ev->steps = steps + 1;
+      return;
+    }
+    double xb[3], D[3];
+    plane_point(pl, pb, un, xb);
+    for (int k = 0; k < 3; ++k) D[k] = xb[k] - xa[k];
+    double best_s = INFINITY;
+    int best = -1; /* 0 sphere, 1 disk */
+    unsigned best_id = 0;
+    /* disk: the segment crosses z = 0 */
+    if (sc->disk_enabled && !pl->disk_in_plane) {
+      double za = xa[2], zb = xb[2];
+      if ((za > 0.0 && zb <= 0.0) || (za < 0.0 && zb >= 0.0)) {
+        double s = za / (za - zb), X[3];
+        for (int k = 0; k < 3; ++k) X[k] = xa[k] + s * D[k];
+        double r = norm3(X);
+        if (fabs(r - sc->disk_r_in) < o->eps_r || fabs(r - sc->disk_r_out) < o->eps_r)
+          ev->ambig |= OR_AMB_DISK;
+        if (r >= sc->disk_r_in && r <= sc->disk_r_out) {
+          best_s = s;
+          best = 1;
+        }
+      }
+    }
+    /* spheres: first entry along the segment */
+    double dd = dot3(D, D);
+    for (int k = 0; k < sc->n_spheres; ++k) {
+      const or_sphere *S = &sc->spheres[k];
+      double oc[3] = {xa[0] - S->c[0], xa[1] - S->c[1], xa[2] - S->c[2]};
+      double bq = dot3(oc, D), cq = dot3(oc, oc) - S->radius * S->radius;
+      /* closest approach of the segment to the centre, for the graze mask */
+      double sc_ = fmin(1.0, fmax(0.0, -bq / dd));
+      double cl[3] = {oc[0] + sc_ * D[0], oc[1] + sc_ * D[1], oc[2] + sc_ * D[2]};
+      if (fabs(norm3(cl) - S->radius) < o->eps_r) ev->ambig |= OR_AMB_SPHERE;
+      double disc = bq * bq - dd * cq;
+      if (disc < 0.0) continue;
+      double s = (-bq - sqrt(disc)) / dd;
+      if (s < 0.0 || s > 1.0) continue;
+      if (s < best_s - 1e-12 || (fabs(s - best_s) <= 1e-12 && (best != 0 || (unsigned)k < best_id))) {
+        best_s = s;
+        best = 0;
+        best_id = (unsigned)k;
+      }
+    }
+    if (best >= 0) {
+      double nD = sqrt(dd);
+      for (int k = 0; k < 3; ++k) {
+        ev->x[k] = xa[k] + best_s * D[k];
+        ev->t[k] = D[k] / nD;
+      }
+      ev->flags = best == 0 ? OR_SPHERE : OR_DISK;
+      ev->sphere_id = best_id;
+      ev->steps = steps + 1;
+      return;
+    }
+    if (un >= u_capt) {
+      ev->flags = OR_CAPT;
+      ev->steps = steps + 1;
+      return;
+    }
+    u = un;
+    v = vn;
+    phi = pb;
+    for (int k = 0; k < 3; ++k) xa[k] = xb[k];
+  }
+}
+
+/* Shade a polyline event into out (direction, colour, mask bits). */
+static void shade_polyline(const or_scene *sc, const or_opts *o, const or_plane *pl,
+                           const or_poly_event *ev, or_pixel *out) {
+  out->ambig |= ev->ambig;
+  out->steps = ev->steps;
+  out->flags = ev->flags;
+  out->sphere_id = ev->sphere_id;
+  if (ev->flags == OR_CAPT || ev->flags == OR_STEP_LIMIT) {
+    out->theta = out->phi = NAN;
+    out->rgb[0] = out->rgb[1] = out->rgb[2] = 0.0;
+    return;
+  }
+  double dirv[3];
+  if (ev->flags == OR_ESC) {
+    double cp = cos(ev->phi_esc), sp = sin(ev->phi_esc);
+    for (int k = 0; k < 3; ++k) dirv[k] = cp * pl->e1[k] + sp * pl->e2[k];
+    dir_angles(dirv, &out->theta, &out->phi);
+    sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
+    if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
+    return;
+  }
+  double r = norm3(ev->x);
+  for (int k = 0; k < 3; ++k) dirv[k] = ev->x[k] / r;
+  dir_angles(dirv, &out->theta, &out->phi);
+  if (ev->flags == OR_DISK) {
+    disk_rgb(sc, r, out->rgb);
+  } else {
+    const or_sphere *S = &sc->spheres[ev->sphere_id];
+    double N[3];
+    for (int k = 0; k < 3; ++k) N[k] = (ev->x[k] - S->c[k]) / S->radius;
+    double lam = 0.25 + 0.75 * fmax(0.0, -dot3(N, ev->t));
+    for (int c = 0; c < 3; ++c) out->rgb[c] = S->albedo[c] * lam;
+  }
+}
+
 static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
                        const double d[3], or_pixel *out) {
   double M = sc->mass;
@@ -687,6 +858,12 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
   }
   if (sc->disk_enabled && pl.disk_in_plane) out->ambig |= OR_AMB_DEGEN;
 
+  if (o->method == 1) {
+    or_poly_event pev;
+    trace_polyline(sc, o, &pl, &pev);
+    shade_polyline(sc, o, &pl, &pev, out);
+    return;
+  }
   or_event ev;
   trace_plane(sc, o, &pl, &ev);
   out->ambig |= ev.ambig;
@@ -705,12 +882,7 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
     sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
     if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
   } else if (ev.flags == OR_DISK) {
-    double r = 1.0 / ev.u_evt;
-    double t = pow(sc->disk_r_in / r, 0.75);
-    double k = 0.3 + 0.7 * t;
-    out->rgb[0] = 1.0 * k;
-    out->rgb[1] = (0.35 + 0.65 * t) * k;
-    out->rgb[2] = (0.1 + 0.9 * t * t) * k;
+    disk_rgb(sc, 1.0 / ev.u_evt, out->rgb);
   } else { /* sphere */
     const or_sphere *S = &sc->spheres[ev.sphere_id];
     double u = ev.u_evt, v = ev.v_evt;

@@ -18,7 +18,8 @@ import ctypes
 from . import _capi
 from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # noqa: F401
                     BH_FLAG_FP64, BH_FLAG_SPHERE, BH_FLAG_STEP_LIMIT, BH_FLAG_SURR,
-                    BH_MODE_FP32, BH_MODE_FP64, BH_MODE_MIXED, BH_MODE_SURROGATE, MODES,
+                    BH_MODE_FP32, BH_MODE_FP64, BH_MODE_MIXED, BH_MODE_PAPER_EPS,
+                    BH_MODE_PAPER_EPS_FP32, BH_MODE_SURROGATE, MODES,
                     BHError, check)
 
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
@@ -337,7 +338,7 @@ class Scene:
         import torch
         n = sum(int(c.w) * int(c.h) for c in cams)
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        dt = torch.float64 if m == BH_MODE_FP64 else torch.float32
+        dt = torch.float64 if m in (BH_MODE_FP64, BH_MODE_PAPER_EPS) else torch.float32
         dev = torch.device("cuda", torch.cuda.current_device())
         if dirs is None:
             dirs = torch.empty(2 * n, dtype=dt, device=dev)

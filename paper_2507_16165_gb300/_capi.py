@@ -18,13 +18,15 @@ BH_OK = 0
 BH_E_INVALID, BH_E_NOMEM, BH_E_CUDA, BH_E_DEVICE = -1, -2, -3, -4
 BH_E_NO_SURROGATE, BH_E_IO, BH_E_UNSUPPORTED = -5, -6, -7
 BH_MODE_FP64, BH_MODE_FP32, BH_MODE_MIXED, BH_MODE_SURROGATE = 0, 1, 2, 3
+BH_MODE_PAPER_EPS, BH_MODE_PAPER_EPS_FP32 = 4, 5
 BH_IC_STATIC, BH_IC_EUCLIDEAN = 0, 1
 BH_FLAG_ESC, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_SPHERE = 1, 2, 4, 8
 BH_FLAG_BAND, BH_FLAG_FP64, BH_FLAG_SURR, BH_FLAG_STEP_LIMIT = 16, 32, 64, 128
 BH_STATUS_ABORTED, BH_STATUS_WATCHDOG = 1, 2
 
 MODES = {"fp64": BH_MODE_FP64, "fp32": BH_MODE_FP32, "mixed": BH_MODE_MIXED,
-         "surrogate": BH_MODE_SURROGATE}
+         "surrogate": BH_MODE_SURROGATE, "paper": BH_MODE_PAPER_EPS,
+         "paper_fp32": BH_MODE_PAPER_EPS_FP32}
 
 
 class bh_sphere(ctypes.Structure):
@@ -56,7 +58,7 @@ class bh_render_opts(ctypes.Structure):
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
-                ("h_max_far", ctypes.c_double)]
+                ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double)]
 
 
 class bh_stats(ctypes.Structure):

@@ -113,7 +113,8 @@ struct Spill {
   R u, v, phi, h;
 };
 
-enum Mode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_MIXED = 2, MODE_BAND64 = 3 };
+enum Mode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_MIXED = 2, MODE_BAND64 = 3, MODE_PAPER32 = 4,
+            MODE_PAPER64 = 5 };
 
 // Kernel parameter block.
 struct Params {
@@ -130,6 +131,7 @@ struct Params {
   double phi_max;
   double h_max;                 // step-size cap of the main pass (FP64 band: none)
   double h_max_far;             // FP32 step cap of rays with |b - b_c| >= kFarB
+  double paper_eps;             // fixed step of the polyline modes
   int max_steps;
   int peri_reset;
   unsigned long long abort_after;  // stop grabbing work past this slot (0 = off)

@@ -216,7 +216,7 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
   if (!sc || !cams || !w || !h || !opts) return bh_fail(BH_E_INVALID, "bh_render: null argument");
   if (n_cams < 1 || n_cams > kMaxCameras)
     return bh_fail(BH_E_INVALID, "bh_render: n_cams must be in [1, %d]", kMaxCameras);
-  if (opts->mode < BH_MODE_FP64 || opts->mode > BH_MODE_SURROGATE)
+  if (opts->mode < BH_MODE_FP64 || opts->mode > BH_MODE_PAPER_EPS_FP32)
     return bh_fail(BH_E_INVALID, "bh_render: unknown mode %d", opts->mode);
   for (int i = 0; i < n_cams; ++i) {
     if (w[i] < 1 || h[i] < 1 || w[i] > 65536 || h[i] > 65536)
@@ -232,7 +232,7 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
       opts->block_size != 256)
     return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
-      opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 ||
+      opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
   return BH_OK;
@@ -276,7 +276,7 @@ int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
 RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   RenderConfig c;
   c.mode = o->mode;
-  const bool f64 = (o->mode == BH_MODE_FP64);
+  const bool f64 = mode_is_fp64(o->mode);
   c.rtol = o->rtol > 0 ? o->rtol : (f64 ? 1e-10 : 1e-5);
   c.atol = o->atol > 0 ? o->atol : (f64 ? 1e-10 : 1e-7);
   c.band = o->band > 0 ? o->band : 0.05;
@@ -285,6 +285,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
   c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
+  c.paper_eps = o->paper_eps > 0 ? o->paper_eps : 0.01;
   const TunedShape t = tuned_shape(sc, o->mode);
   c.block = o->block_size ? o->block_size : t.block;
   c.blocks_per_sm = o->blocks_per_sm ? o->blocks_per_sm : t.blocks_per_sm;
@@ -314,7 +315,7 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
     cams_dev = sc->d_cams;
   }
   if (e == cudaSuccess) e = grow(&sc->d_band, &sc->band_cap, (size_t)n_queue);
-  const size_t spill_bytes = (cfg.mode == BH_MODE_FP64 ? sizeof(Spill<double>) : sizeof(Spill<float>));
+  const size_t spill_bytes = (mode_is_fp64(cfg.mode) ? sizeof(Spill<double>) : sizeof(Spill<float>));
   if (e == cudaSuccess) e = grow(&sc->d_spill, &sc->spill_cap, (size_t)n_queue * spill_bytes);
   if (e == cudaSuccess && cfg.mode == BH_MODE_MIXED)
     e = grow(&sc->d_bits, &sc->bits_cap, (size_t)(n_queue / 32 + 1));
@@ -335,7 +336,11 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
     ls.band_warps = cfg.band_warps;
   }
   out->ls = ls;
-  out->kmode = cfg.mode == BH_MODE_FP64 ? MODE_FP64 : cfg.mode == BH_MODE_FP32 ? MODE_FP32 : MODE_MIXED;
+  out->kmode = cfg.mode == BH_MODE_FP64             ? MODE_FP64
+               : cfg.mode == BH_MODE_FP32           ? MODE_FP32
+               : cfg.mode == BH_MODE_PAPER_EPS      ? MODE_PAPER64
+               : cfg.mode == BH_MODE_PAPER_EPS_FP32 ? MODE_PAPER32
+                                                    : MODE_MIXED;
   out->mode = cfg.mode;
   return BH_OK;
 }
@@ -387,6 +392,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.phi_max = cfg.phi_max;
   p.h_max = cfg.h_max;
   p.h_max_far = cfg.h_max_far;
+  p.paper_eps = cfg.paper_eps;
   p.max_steps = cfg.max_steps;
   p.peri_reset = cfg.peri_reset;
   p.abort_after = cfg.abort_after;
@@ -427,7 +433,7 @@ extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int 
   long long n = 0;
   for (int i = 0; i < n_cams; ++i) n += (long long)w[i] * h[i];
   if (n >= 0x7FFFFFFFLL) return bh_fail(BH_E_INVALID, "bh_render_host: too many rays");
-  const size_t dsz = opts->mode == BH_MODE_FP64 ? sizeof(double) : sizeof(float);
+  const size_t dsz = mode_is_fp64(opts->mode) ? sizeof(double) : sizeof(float);
   cudaError_t e = grow((char**)&sc->d_stage_dirs, &sc->stage_dirs_cap, (size_t)(2 * n) * dsz);
   if (e == cudaSuccess) e = grow(&sc->d_stage_flags, &sc->stage_flags_cap, (size_t)n);
   if (e == cudaSuccess) e = grow(&sc->d_stage_rgba, &sc->stage_rgba_cap, (size_t)n);

@@ -692,6 +692,206 @@ __global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Pa
 }
 
 // ---------------------------------------------------------------------------
+// The paper's own stepping (Sec. 2.1-2.2, Fig. 1), kept as a mode to measure
+// it against the adaptive path: points of the ray at fixed steps eps in phi
+// from the classical fourth-order Runge-Kutta method, joined by straight
+// segments; objects are found by intersecting each segment with them.  The
+// segments lie in the orbital plane, so the work is done in its 2-D
+// coordinates (x, y) = (cos phi, sin phi) / u.  A step whose end has u <= 0
+// escapes along the angle where the line between the last two (phi, u)
+// reaches u = 0; a segment ending at u >= 1/(2M) that meets no object is
+// captured.  The points are only formed for steps that may meet an object
+// (a disk node or a sphere's angular window inside the step).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void rk4_step(R M3, R h, R& u, R& v) {
+  const R hh = R(0.5) * h;
+  const R k1 = accel(M3, u);
+  const R v2 = m_fma(hh, k1, v);
+  const R k2 = accel(M3, m_fma(hh, v, u));
+  const R v3 = m_fma(hh, k2, v);
+  const R k3 = accel(M3, m_fma(hh, v2, u));
+  const R v4 = m_fma(h, k3, v);
+  const R k4 = accel(M3, m_fma(h, v3, u));
+  const R h6 = h * R(1.0 / 6.0);
+  const R un = m_fma(h6, v + R(2) * (v2 + v3) + v4, u);
+  v = m_fma(h6, k1 + R(2) * (k2 + k3) + k4, v);
+  u = un;
+}
+
+template <typename R>
+__device__ __forceinline__ void plane_xy(R phi, R u, R* x, R* y) {
+  R s, c;
+  m_sincos_evt(phi, &s, &c);
+  const R ir = m_div(R(1), u);
+  *x = c * ir;
+  *y = s * ir;
+}
+
+// Objects met by the segment from (xa, ya) to (xb, yb): the smallest
+// parameter s in [0, 1] of a disk crossing (z = x e1z + y e2z changes sign,
+// radius inside the annulus) or a sphere entry (the sphere's circle in the
+// plane).  Returns the event type (-1 for none), *s and the sphere id.
+template <typename R>
+__device__ int segment_objects(const Params& p, const Ray<R>& r, R xa, R ya, R xb, R yb,
+                               bool disk, unsigned sph, R* s_out, unsigned* id_out) {
+  const SceneR<R>& S = SR<R>(p.s);
+  int best = -1;
+  R best_s = R(INFINITY);
+  const R dx = xb - xa, dy = yb - ya;
+  if (disk) {
+    const R za = xa * r.e1z + ya * r.e2z, zb = xb * r.e1z + yb * r.e2z;
+    if ((za > R(0) && zb <= R(0)) || (za < R(0) && zb >= R(0))) {
+      const R s = m_div(za, za - zb);
+      const R X = m_fma(s, dx, xa), Y = m_fma(s, dy, ya);
+      const R rr = m_sqrt(m_fma(X, X, Y * Y));
+      if (rr >= S.r_in && rr <= S.r_out) {
+        best = EV_DISK;
+        best_s = s;
+      }
+    }
+  }
+  const R dd = m_fma(dx, dx, dy * dy);
+  while (sph) {
+    const int k = __ffs(sph) - 1;
+    sph &= sph - 1;
+    const R c0 = S.c[k][0], c1 = S.c[k][1], c2 = S.c[k][2];
+    const R cx = c0 * r.e1x + c1 * r.e1y + c2 * r.e1z;
+    const R cy = c0 * r.e2x + c1 * r.e2y + c2 * r.e2z;
+    const R rp2 = S.rad[k] * S.rad[k] - (S.c2[k] - (cx * cx + cy * cy));  // circle radius^2
+    const R ox = xa - cx, oy = ya - cy;
+    const R bq = m_fma(ox, dx, oy * dy);
+    const R cq = m_fma(ox, ox, oy * oy) - rp2;
+    const R disc = bq * bq - dd * cq;
+    if (!(disc >= R(0))) continue;
+    const R s = m_div(-bq - m_sqrt(disc), dd);
+    if (s < R(0) || s > R(1)) continue;
+    if (s < best_s || (s == best_s && best != EV_SPHERE)) {
+      best = EV_SPHERE;
+      best_s = s;
+      *id_out = (unsigned)k;
+    }
+  }
+  *s_out = best_s;
+  return best;
+}
+
+// One fixed step of the polyline method.  Returns true when the ray ended
+// (hit filled in for finish_ray: the hit point's plane angle, u = 1/|X| and
+// a u' that makes finish_ray's tangent the segment's direction).
+template <typename R>
+__device__ __forceinline__ bool paper_step(const Params& p, Ray<R>& r, R eps, R u_capt, Hit<R>& hit,
+                                           LocalStats& st) {
+  const SceneR<R>& S = SR<R>(p.s);
+  R un = r.u, vn = r.v;
+  rk4_step<R>(S.M3, eps, un, vn);
+  r.steps++;
+  st.c[ST_STEPS]++;
+  if (sizeof(R) == 8) st.c[ST_STEPS64]++;
+  const R pa = r.phi, pb = pa + eps;
+  if (un <= R(0)) {
+    hit.flags = BH_FLAG_ESC;
+    hit.phi = m_fma(eps, m_div(r.u, r.u - un), pa);
+    hit.u = R(0);
+    hit.v = R(0);
+    return true;
+  }
+  const bool disk = p.s.disk_on && r.phi_node <= pb;
+  unsigned sph = 0;
+  if (pb >= r.phi_sph) {
+    unsigned m = r.sph_mask;
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1;
+      float we;
+      const float ws = sphere_window(r, k, (float)pa, &we);
+      if (R(ws) <= pb && R(we) >= pa) sph |= 1u << k;
+    }
+  }
+  if (disk || sph) {
+    st.c[ST_EVENTS]++;
+    R xa, ya, xb, yb;
+    plane_xy<R>(pa, r.u, &xa, &ya);
+    plane_xy<R>(pb, un, &xb, &yb);
+    R s;
+    unsigned id = 0;
+    const int ev = segment_objects<R>(p, r, xa, ya, xb, yb, disk, sph, &s, &id);
+    while (r.phi_node <= pb) r.phi_node += Num<R>::pi;
+    if (sph) r.phi_sph = next_sphere_window<R>(r, pb);
+    if (ev >= 0) {
+      const R dx = xb - xa, dy = yb - ya;
+      const R X = m_fma(s, dx, xa), Y = m_fma(s, dy, ya);
+      const R rr = m_sqrt(m_fma(X, X, Y * Y));
+      // the hit angle, continued from pa so that phi mod 2 pi is exact
+      const R ph = pa + m_atan2(xa * Y - ya * X, xa * X + ya * Y);
+      const R u = m_div(R(1), rr);
+      const R cr = m_div(X, rr), sr = m_div(Y, rr);
+      const R along = m_fma(dx, cr, dy * sr), across = m_fma(dy, cr, -dx * sr);
+      hit.flags = ev == EV_DISK ? BH_FLAG_DISK : (BH_FLAG_SPHERE | (id << 8));
+      hit.phi = ph;
+      hit.u = u;
+      hit.v = across != R(0) ? -u * m_div(along, across) : R(0);
+      return true;
+    }
+  }
+  if (un >= u_capt) {
+    hit.flags = BH_FLAG_CAPT;
+    hit.phi = pb;
+    hit.u = un;
+    hit.v = vn;
+    return true;
+  }
+  r.u = un;
+  r.v = vn;
+  r.phi = pb;
+  if (r.steps >= p.max_steps || pb >= TolPick<R, sizeof(R) == 8 ? MODE_FP64 : MODE_FP32>::get(p).phi_max) {
+    hit.flags = BH_FLAG_STEP_LIMIT;
+    hit.phi = pb;
+    hit.u = un;
+    hit.v = vn;
+    return true;
+  }
+  return false;
+}
+
+template <typename R, typename OutR>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_paper(const __grid_constant__ Params p) {
+  constexpr int MODE = sizeof(R) == 8 ? MODE_FP64 : MODE_FP32;
+  const int lane = threadIdx.x & 31;
+  const R eps = R(p.paper_eps);
+  const R u_capt = SR<R>(p.s).M > R(0) ? R(0.5) / SR<R>(p.s).M : R(INFINITY);
+  LocalStats st;
+  st.zero();
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ws->q_next, 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned long long)p.n_queue) break;
+    if (p.abort_after && base >= p.abort_after) {
+      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
+      break;
+    }
+    if (lane == 0) st.c[ST_GRABS]++;
+    const long long q = (long long)base + lane;
+    Ray<R> r;
+    R b;
+    bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
+    if (active) r.steps = 0;
+    while (__any_sync(kFull, active)) {
+      if (active) {
+        Hit<R> hit;
+        if (paper_step<R>(p, r, eps, u_capt, hit, st)) {
+          finish_ray<R, OutR>(p, r, hit);
+          st.count_flag(hit.flags | r.aux);
+          active = false;
+        }
+      }
+    }
+  }
+  st.flush(p.ws);
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch.
 // ---------------------------------------------------------------------------
 template <typename K>
@@ -725,7 +925,18 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     if (ev && ev[i]) record(ev[i], stream);
   };
   rec(0);
-  if (mode == MODE_FP64) {
+  if (mode == MODE_PAPER32 || mode == MODE_PAPER64) {
+    if (mode == MODE_PAPER64) {
+      auto k = k_paper<double, double>;
+      k<<<grid_of(k), block, 0, stream>>>(p);
+    } else {
+      auto k = k_paper<float, float>;
+      k<<<grid_of(k), block, 0, stream>>>(p);
+    }
+    rec(1);
+    rec(2);
+    rec(3);
+  } else if (mode == MODE_FP64) {
     auto k1 = k_coherent<double, MODE_FP64, double>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);

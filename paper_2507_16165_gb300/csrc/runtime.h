@@ -48,7 +48,7 @@ struct bh_scene {
 // Resolved options of one render.
 struct RenderConfig {
   int mode;
-  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far;
+  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, paper_eps;
   int max_steps;
   int block, blocks_per_sm, tile_w, tile_h, budget;
   int band_lanes, band_warps;
@@ -78,6 +78,8 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
 int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                   int tw, int th, long long* n_queue, long long* n_rays);
 RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o);
+// Modes whose directions are stored as double.
+inline bool mode_is_fp64(int mode) { return mode == BH_MODE_FP64 || mode == BH_MODE_PAPER_EPS; }
 void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long long n_queue,
                  long long n_rays, void* dirs, uint16_t* flags, uint32_t* rgba, bhk::Params* out);
 void fill_tolerances(bhk::Params& p);

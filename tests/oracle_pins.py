@@ -491,3 +491,69 @@ ALL = [first_integral, exit_angle, exit_angle_render_tol, weak_field,
        straight_lines_m0, disk_m0, spheres_m0, shadow_edge, einstein_ring,
        disk_radius_m1, splitmix_vector, sky_cells, camera_convention,
        b_matches_v0, hits_on_surfaces_m1, disk_colour_ends]
+
+
+# --- the paper's fixed-step polyline (method 1; Sec. 2.1-2.2) ------------
+
+def _gc(t1, p1, t2, p2):
+    a = np.stack([np.sin(t1) * np.cos(p1), np.sin(t1) * np.sin(p1), np.cos(t1)], -1)
+    b = np.stack([np.sin(t2) * np.cos(p2), np.sin(t2) * np.sin(p2), np.cos(t2)], -1)
+    return np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, -1))
+
+
+def polyline_straight_m0(lib):
+    """At M = 0 the Runge-Kutta points lie on the straight ray to O(eps^4),
+    so do the segments: escapes leave along the camera direction and disk
+    hits are the ray-plane intersection (1e-7 rad)."""
+    from dataclasses import replace
+    w = W.config2(24, "fp64")
+    w = replace(w, scene=replace(w.scene, mass=0.0))
+    cam = w.cameras[0]
+    got = oracle.render(w.scene, w.cameras, oracle.opts(eps=0.01, method=oracle.METHOD_POLYLINE),
+                        lib=lib)
+    worst, n_disk = 0.0, 0
+    for idx in range(cam.w * cam.h):
+        P, d = oracle.camera_ray(cam, idx % cam.w, idx // cam.w, lib=lib)
+        fl = got["flags"][idx] & 0xFF
+        th, ph = got["theta"][idx], got["phi"][idx]
+        dd = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        if fl == oracle.ESC:
+            worst = max(worst, angle_between(dd, d))
+        elif fl == oracle.DISK:
+            X = P - P[2] / d[2] * d
+            worst = max(worst, angle_between(dd, X))
+            n_disk += 1
+    return worst < 1e-7 and n_disk > 20, f"worst {worst:.2e} rad over {n_disk} disk hits"
+
+
+def polyline_nodes(lib):
+    """A segment crosses the disk plane on the line of nodes, so polyline
+    disk hits point exactly where the adaptive method's do (1e-9 rad)."""
+    w = W.config2(40, "fp64")
+    ref = oracle.render(w.scene, w.cameras, oracle.opts(), lib=lib)
+    got = oracle.render(w.scene, w.cameras, oracle.opts(eps=0.02, method=oracle.METHOD_POLYLINE),
+                        lib=lib)
+    both = ((got["flags"] & 0xFF) == oracle.DISK) & ((ref["flags"] & 0xFF) == oracle.DISK)
+    ang = _gc(got["theta"][both], got["phi"][both], ref["theta"][both], ref["phi"][both])
+    mx = float(ang.max()) if both.any() else 1.0
+    return both.sum() > 100 and mx < 1e-9, f"{int(both.sum())} disk hits, max {mx:.2e} rad"
+
+
+def polyline_escape_order(lib):
+    """The escape angle's error against the adaptive method falls at third
+    order in eps (classical Runge-Kutta points, linear interpolation of u
+    where u'' vanishes with u): median ratios above 5.5 per halving."""
+    w = W.config1(32)
+    ref = oracle.render(w.scene, w.cameras, oracle.opts(), lib=lib)
+    med = []
+    for eps in (0.04, 0.02, 0.01):
+        got = oracle.render(w.scene, w.cameras, oracle.opts(eps=eps, method=oracle.METHOD_POLYLINE),
+                            lib=lib)
+        esc = ((got["flags"] & 0xFF) == oracle.ESC) & ((ref["flags"] & 0xFF) == oracle.ESC)
+        ang = _gc(got["theta"][esc], got["phi"][esc], ref["theta"][esc], ref["phi"][esc])
+        med.append(float(np.median(ang)) if esc.any() else 1.0)
+    ok = all(c / f > 5.5 for c, f in zip(med, med[1:])) and med[-1] < 1e-7
+    return ok, "medians " + ", ".join(f"{m:.2e}" for m in med)
+
+
+POLYLINE = [polyline_straight_m0, polyline_nodes, polyline_escape_order]

@@ -44,6 +44,15 @@ MUTANTS = [
      "double t = pow(r / sc->disk_r_in, 0.75);", [P.disk_colour_ends]),
     ("sphere_normal_sign", "double lam = 0.25 + 0.75 * fmax(0.0, -dot3(N, T));",
      "double lam = 0.25 + 0.75 * fmax(0.0, dot3(N, T));", [P.hits_on_surfaces_m1, P.spheres_m0]),
+    # the paper's polyline method
+    ("rk4_weight", "*u = u0 + h / 6.0 * (ku1 + 2.0 * ku2 + 2.0 * ku3 + ku4);",
+     "*u = u0 + h / 6.0 * (ku1 + 2.0 * ku2 + 1.0 * ku3 + 2.0 * ku4);", [P.polyline_escape_order]),
+    ("rk4_half_step", "double ku3 = v0 + 0.5 * h * kv2, kv3 = accel(M, u0 + 0.5 * h * ku2);",
+     "double ku3 = v0 + 0.5 * h * kv2, kv3 = accel(M, u0 + h * ku2);", [P.polyline_escape_order]),
+    ("escape_interpolation_end", "ev->phi_esc = phi + eps * u / (u - un);",
+     "ev->phi_esc = phi + eps * un / (u - un);", [P.polyline_straight_m0, P.polyline_escape_order]),
+    ("segment_plane_parameter", "double s = za / (za - zb), X[3];", "double s = zb / (za - zb), X[3];",
+     [P.polyline_straight_m0, P.polyline_nodes]),
 ]
 
 
