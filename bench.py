@@ -293,7 +293,9 @@ def run_ours(args) -> None:
     rgba = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band,
-                          paper_eps=args.paper_eps)
+                          paper_eps=args.paper_eps, spp=args.spp)
+    # rays traced per pixel: n x n samples plus the centre ray when anti-aliased
+    rays_per_pixel = args.spp + 1 if args.spp > 1 else 1
 
     surrogate = None
     if args.form == "surrogate":
@@ -346,7 +348,7 @@ def run_ours(args) -> None:
     bh.bh_scene_sync(sc.handle)
     ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, "cuda")
     ms_per_step = ms / args.steps
-    value = job_rate(n, args.steps, world, ms * 1e-3)
+    value = job_rate(n * rays_per_pixel, args.steps, world, ms * 1e-3)
 
     # roofline: the integrator kernels (coherent + long-ray passes) against
     # the FP32 pipe, or the FP64 pipe in the FP64 form
@@ -391,7 +393,7 @@ def run_ours(args) -> None:
         dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         import ctypes
         from paper_2507_16165_gb300 import _capi
-        e2e = {"value": job_rate(n, args.steps, world, dt), "unit": UNIT,
+        e2e = {"value": job_rate(n * rays_per_pixel, args.steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": len(cams) * (ctypes.sizeof(_capi.bh_camera) + 8),
                "d2h_bytes_per_step": n * (dirs.element_size() * 2 + 2 + 4)}
 
@@ -419,6 +421,8 @@ def run_ours(args) -> None:
                    "rtol": w.rtol, "atol": w.atol,
                    "band": w.band, "stated_exit_dir_error_rad": STATED_ERROR[args.form],
                    "paper_eps": args.paper_eps if paper else None,
+                   "spp": args.spp if args.spp > 1 else None,
+                   "mpixels_per_s": job_rate(n, args.steps, world, ms * 1e-3),
                    "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps (outside the events)",
                    "launch": ("autotuned shape, one CUDA-graph replay per step: " + json.dumps(tuned))
@@ -436,7 +440,7 @@ def run_ours(args) -> None:
                                     served_bins=surrogate["calibration"]["served_bins"],
                                     served_rays_fraction=stats["n_surrogate"] / n)
                                if surrogate else None),
-        "steps_per_ray": steps_all / args.steps / n,
+        "steps_per_ray": steps_all / args.steps / (n * rays_per_pixel),
         "wall_s": t_wall,
         "stats_last": {k: stats[k] for k in ("rays", "n_band", "n_long", "periastron", "n_capt",
                                              "n_disk", "n_sphere", "n_esc", "n_surrogate",
@@ -455,6 +459,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate", "paper", "paper_fp32"),
                     default="mixed")
+    ap.add_argument("--spp", type=int, default=1,
+                    help="samples per pixel (a square; fp32 and fp64 forms)")
     ap.add_argument("--paper-eps", type=float, default=0.01,
                     help="fixed step of the paper's own stepping forms (rad)")
     ap.add_argument("--size", type=int, default=4096)

@@ -151,6 +151,14 @@ typedef struct bh_render_opts {
                          sensitive to stepping errors (0: 0.4; FP64: h_max) */
   double paper_eps;   /* fixed step in rad of the BH_MODE_PAPER_EPS modes
                          (0: 0.01)                                          */
+  int spp;            /* samples per pixel, a square n*n (0 or 1: one ray
+                         through the pixel centre).  With n > 1 the n x n
+                         stratified sub-pixel samples (centres of an n x n
+                         grid over the pixel) are averaged in linear colour
+                         into RGBA8 (box filter) and one more ray through
+                         the pixel centre gives its direction and flags.
+                         BH_MODE_FP32 and BH_MODE_FP64 only (else
+                         BH_E_UNSUPPORTED); n <= 16                          */
 } bh_render_opts;
 
 typedef struct bh_stats {

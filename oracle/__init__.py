@@ -60,7 +60,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("phi_max", ctypes.c_double), ("max_steps", ctypes.c_long),
                 ("eps_r", ctypes.c_double), ("eps_ang", ctypes.c_double),
-                ("eps_b", ctypes.c_double), ("method", ctypes.c_int), ("eps", ctypes.c_double)]
+                ("eps_b", ctypes.c_double), ("method", ctypes.c_int), ("eps", ctypes.c_double),
+                ("spp_n", ctypes.c_int)]
 
 
 METHOD_DP5 = 0
@@ -146,10 +147,11 @@ def _cams(cams) -> ctypes.Array:
 
 
 def opts(rtol=1e-10, atol=1e-10, phi_max=64.0, max_steps=100000,
-         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6, method=METHOD_DP5, eps=0.01) -> _Opts:
+         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6, method=METHOD_DP5, eps=0.01, spp_n=1) -> _Opts:
     """Integration tolerances, caps and ambiguity thresholds; method 1 is the
-    paper's fixed-step polyline with step eps (Sec. 2.1-2.2)."""
-    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b, method, eps)
+    paper's fixed-step polyline with step eps (Sec. 2.1-2.2); spp_n > 1
+    averages n x n stratified samples per pixel into its colour."""
+    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b, method, eps, spp_n)
 
 
 def _ptr(a: np.ndarray) -> int:

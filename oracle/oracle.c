@@ -85,6 +85,7 @@ typedef struct {
   int method;  /* 0: Dormand-Prince 5(4) with exact events; 1: the paper's
                   fixed-step polyline (Sec. 2.1-2.2) */
   double eps;  /* step in phi of method 1 */
+  int spp_n;   /* samples per pixel side: n x n stratified samples (<= 1: one) */
 } or_opts;
 
 typedef struct {
@@ -904,6 +905,35 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
   (void)M;
 }
 
+/* One pixel.  With spp_n = n > 1 the pixel's colour is the mean of the
+ * linear colours of n x n stratified samples, at the centres of an n x n
+ * grid over the pixel (anti-aliasing, Sec. 3); its direction, flags, impact
+ * parameter and step count are those of the ray through the pixel centre,
+ * and its mask collects the bits of every sample. */
+static void render_pixel(const or_scene *sc, const or_opts *o, const or_camera *cam, int x, int y,
+                         or_pixel *out) {
+  double P[3], d[3];
+  camera_ray(cam, x, y, P, d);
+  render_ray(sc, o, P, d, out);
+  int n = o->spp_n;
+  if (n <= 1) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  unsigned amb = out->ambig;
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) {
+      /* camera_ray adds half a pixel to its coordinates */
+      double sx = x + (i + 0.5) / n - 0.5, sy = y + (j + 0.5) / n - 0.5;
+      camera_ray(cam, sx, sy, P, d);
+      or_pixel smp;
+      render_ray(sc, o, P, d, &smp);
+      for (int c = 0; c < 3; ++c) acc[c] += smp.rgb[c];
+      amb |= smp.ambig;
+    }
+  }
+  for (int c = 0; c < 3; ++c) out->rgb[c] = acc[c] / (n * n);
+  out->ambig = amb;
+}
+
 static void store_pixel(const or_pixel *px, long idx, double *theta, double *phi,
                         uint16_t *flags, uint32_t *rgba, uint8_t *ambig,
                         double *b_out, int32_t *steps_out) {
@@ -951,10 +981,8 @@ int or_render(const or_scene *sc, const or_camera *cams, int ncams,
 #pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < Hh; ++y) {
       for (int x = 0; x < W; ++x) {
-        double P[3], d[3];
-        camera_ray(cam, x, y, P, d);
         or_pixel px;
-        render_ray(sc, o, P, d, &px);
+        render_pixel(sc, o, cam, x, y, &px);
         store_pixel(&px, base + (long)y * W + x, theta, phi, flags, rgba, ambig,
                     b_out, steps_out);
       }
@@ -982,10 +1010,8 @@ int or_render_pixels(const or_scene *sc, const or_camera *cams, int ncams,
       bad = 1;
       continue;
     }
-    double P[3], d[3];
-    camera_ray(&cams[c], px[i], py[i], P, d);
     or_pixel pxo;
-    render_ray(sc, o, P, d, &pxo);
+    render_pixel(sc, o, &cams[c], px[i], py[i], &pxo);
     store_pixel(&pxo, i, theta, phi, flags, rgba, ambig, b_out, steps_out);
   }
   return bad ? -1 : 0;

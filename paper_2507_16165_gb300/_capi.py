@@ -58,7 +58,8 @@ class bh_render_opts(ctypes.Structure):
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
-                ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double)]
+                ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double),
+                ("spp", ctypes.c_int)]
 
 
 class bh_stats(ctypes.Structure):

@@ -233,8 +233,16 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
     return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
       opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 ||
-      opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0)
+      opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0 || opts->spp < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
+  if (opts->spp > 1) {
+    int n = 1;
+    while (n * n < opts->spp) ++n;
+    if (n * n != opts->spp || n > 16)
+      return bh_fail(BH_E_INVALID, "bh_render: spp must be a square n*n with n <= 16 (got %d)", opts->spp);
+    if (opts->mode != BH_MODE_FP32 && opts->mode != BH_MODE_FP64)
+      return bh_fail(BH_E_UNSUPPORTED, "bh_render: spp > 1 needs BH_MODE_FP32 or BH_MODE_FP64");
+  }
   return BH_OK;
 }
 
@@ -286,12 +294,15 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
   c.paper_eps = o->paper_eps > 0 ? o->paper_eps : 0.01;
+  c.spp_n = 1;
+  while (c.spp_n * c.spp_n < o->spp) ++c.spp_n;
   const TunedShape t = tuned_shape(sc, o->mode);
   c.block = o->block_size ? o->block_size : t.block;
   c.blocks_per_sm = o->blocks_per_sm ? o->blocks_per_sm : t.blocks_per_sm;
   c.tile_w = o->tile_w ? o->tile_w : t.tile_w;
   c.tile_h = o->tile_h ? o->tile_h : t.tile_h;
   c.budget = o->budget ? o->budget : t.budget;
+  if (c.spp_n > 1) c.budget = c.max_steps;  // every sample finishes in the tile pass
   c.band_lanes = t.band_lanes;
   c.band_warps = t.band_warps;
   c.peri_reset = o->periastron_reset >= 0 ? 1 : 0;
@@ -393,6 +404,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.h_max = cfg.h_max;
   p.h_max_far = cfg.h_max_far;
   p.paper_eps = cfg.paper_eps;
+  p.spp_n = cfg.spp_n;
   p.max_steps = cfg.max_steps;
   p.peri_reset = cfg.peri_reset;
   p.abort_after = cfg.abort_after;

@@ -94,9 +94,9 @@ __device__ __forceinline__ bool slot_pixel(const Params& p, long long q, int* ca
 // intersection, otherwise capture (ingoing) or escape along d.  At most a
 // pixel or two per image: kept out of line so it does not crowd the hot
 // code of the persistent kernels (measured 3% faster FP32, 7% mixed).
-template <typename R, typename OutR>
+template <typename R, typename OutR, bool SPP = false>
 __device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a, int out,
-                           unsigned aux, LocalStats& st) {
+                           unsigned aux, LocalStats& st, SppAcc* acc = nullptr) {
   const SceneK& s = p.s;
   const SceneR<R>& S = SR<R>(s);
   R best = R(INFINITY);
@@ -127,16 +127,19 @@ __device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d
     R th, ph;
     dir_angles(x0 * ix, x1 * ix, x2 * ix, &th, &ph);
     flags = BH_FLAG_SPHERE | ((unsigned)bk << 8) | aux;
-    store_ray<OutR>(p, out, OutR(th), OutR(ph), flags,
-                    pack_rgba(s.alb[bk][0] * lam, s.alb[bk][1] * lam, s.alb[bk][2] * lam));
+    const float c[3] = {s.alb[bk][0] * lam, s.alb[bk][1] * lam, s.alb[bk][2] * lam};
+    emit_ray<OutR, SPP>(p, out, OutR(th), OutR(ph), flags, c, acc);
   } else if (ingoing && S.M > R(0)) {
     flags = BH_FLAG_CAPT | aux;
-    store_ray<OutR>(p, out, OutR(NAN), OutR(NAN), flags, 255u << 24);
+    const float c[3] = {0.0f, 0.0f, 0.0f};
+    emit_ray<OutR, SPP>(p, out, OutR(NAN), OutR(NAN), flags, c, acc);
   } else {
     R th, ph;
     dir_angles(d[0], d[1], d[2], &th, &ph);
     flags = BH_FLAG_ESC | aux;
-    store_ray<OutR>(p, out, OutR(th), OutR(ph), flags, sky_rgba<R>(s.seed, th, ph));
+    float c[3];
+    sky_rgb<R>(s.seed, th, ph, c);
+    emit_ray<OutR, SPP>(p, out, OutR(th), OutR(ph), flags, c, acc);
   }
   st.count_flag(flags);
 }
@@ -181,20 +184,21 @@ __device__ __forceinline__ float periastron64(float M, double m2, float v0f, dou
 // Set up the ray of queue slot q.  Returns true when the ray is to be
 // integrated by the caller; false when it was padding, finished directly
 // (radial) or deferred to the FP64 band list.
-template <typename R, int MODE, typename OutR>
-__device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out) {
+template <typename R, int MODE, typename OutR, bool SPP = false>
+__device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out,
+                           R ox = R(0.5), R oy = R(0.5), SppAcc* acc = nullptr) {
   if (MODE == MODE_MIXED && p.band_bits && ((p.band_bits[q >> 5] >> (q & 31)) & 1u)) return false;
   int cam, px, py, out;
   if (!slot_pixel(p, q, &cam, &px, &py, &out)) return false;
   const CamK& c = p.cams[cam];
   R P[3], d[3];
-  camera_ray<R>(c, px, py, P, d);
+  camera_ray<R>(c, px, py, P, d, ox, oy);
   r.out = out;
   r.aux = (MODE == MODE_FP64 || MODE == MODE_BAND64) ? BH_FLAG_FP64 : 0u;
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
   if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, CR<R>(c).ir, r, &b, &cos_a)) {
-    radial_ray<R, OutR>(p, P, d, cos_a, out, r.aux, st);
+    radial_ray<R, OutR, SPP>(p, P, d, cos_a, out, r.aux, st, acc);
     return false;
   }
   *b_out = b;
@@ -445,14 +449,14 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
 // The lanes of a warp integrate their rays in lock step until each has
 // ended (finished and stored) or used its step budget (moved to the
 // long-ray list).
-template <typename R, int MODE, typename OutR>
+template <typename R, int MODE, typename OutR, bool SPP = false>
 __device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool active, long long q,
-                                               LocalStats& st) {
+                                               LocalStats& st, SppAcc* acc = nullptr) {
   while (__any_sync(kFull, active)) {
     if (active) {
       Hit<R> hit;
       if (advance<R, MODE>(p, r, hit, st)) {
-        finish_ray<R, OutR>(p, r, hit);
+        finish_ray<R, OutR, SPP>(p, r, hit, acc);
         st.count_flag(hit.flags | r.aux);
         active = false;
       } else if (r.steps >= p.budget) {
@@ -479,7 +483,7 @@ __device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool 
 // spill a few words but run 2% faster than at 80 with three blocks.
 template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
 
-template <typename R, int MODE, typename OutR>
+template <typename R, int MODE, typename OutR, bool SPP = false>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
   const int lane = threadIdx.x & 31;
   LocalStats st;
@@ -495,10 +499,37 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
     }
     if (lane == 0) st.c[ST_GRABS]++;
     const long long q = (long long)base + lane;
-    Ray<R> r;
-    R b;
-    bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
-    integrate_warp<R, MODE, OutR>(p, r, active, q, st);
+    if (!SPP) {
+      Ray<R> r;
+      R b;
+      bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
+      integrate_warp<R, MODE, OutR>(p, r, active, q, st);
+    } else {
+      // n x n stratified samples per pixel, then the ray through the centre
+      // (directions and flags); every ray of the pixel stays in this lane,
+      // and the lanes take sample k of their pixels together
+      const int n = p.spp_n, ns = n * n;
+      const R inv_n = R(1) / R(n);
+      SppAcc acc;
+      acc.c[0] = acc.c[1] = acc.c[2] = 0.0f;
+      int out = -1;
+      for (int k = 0; k <= ns; ++k) {
+        acc.centre = (k == ns);
+        const R ox = acc.centre ? R(0.5) : (R(k % n) + R(0.5)) * inv_n;
+        const R oy = acc.centre ? R(0.5) : (R(k / n) + R(0.5)) * inv_n;
+        Ray<R> r;
+        R b;
+        r.out = -1;
+        bool active =
+            (q < p.n_queue) && setup_slot<R, MODE, OutR, true>(p, q, r, st, &b, ox, oy, &acc);
+        if (r.out >= 0) out = r.out;
+        integrate_warp<R, MODE, OutR, true>(p, r, active, q, st, &acc);
+      }
+      if (out >= 0 && p.rgba) {
+        const float w = 1.0f / (float)ns;
+        p.rgba[out] = pack_rgba(acc.c[0] * w, acc.c[1] * w, acc.c[2] * w);
+      }
+    }
   }
   st.flush(p.ws);
 }
@@ -931,6 +962,18 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
       k<<<grid_of(k), block, 0, stream>>>(p);
     } else {
       auto k = k_paper<float, float>;
+      k<<<grid_of(k), block, 0, stream>>>(p);
+    }
+    rec(1);
+    rec(2);
+    rec(3);
+  } else if (p.spp_n > 1) {
+    // several samples per pixel: every ray finishes in the tile pass
+    if (mode == MODE_FP64) {
+      auto k = k_coherent<double, MODE_FP64, double, true>;
+      k<<<grid_of(k), block, 0, stream>>>(p);
+    } else {
+      auto k = k_coherent<float, MODE_FP32, float, true>;
       k<<<grid_of(k), block, 0, stream>>>(p);
     }
     rec(1);

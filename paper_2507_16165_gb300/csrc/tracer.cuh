@@ -384,12 +384,14 @@ struct Hit {
   R u, v;          // state at the event
 };
 
-// Camera ray through pixel (px, py) (pixel centres, row 0 at the top).
+// Camera ray through the image point (px + ox, py + oy), by default the
+// centre of pixel (px, py); row 0 is at the top.
 template <typename R>
-__device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3], R d[3]) {
+__device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3], R d[3],
+                                           R ox = R(0.5), R oy = R(0.5)) {
   const CamR<R>& C = CR<R>(c);
-  const R sx = m_fma(R(px) + R(0.5), C.px_scale, -C.sx);
-  const R sy = m_fma(-(R(py) + R(0.5)), C.py_scale, C.sy);
+  const R sx = m_fma(R(px) + ox, C.px_scale, -C.sx);
+  const R sy = m_fma(-(R(py) + oy), C.py_scale, C.sy);
   R dd[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -644,14 +646,13 @@ __device__ __forceinline__ unsigned pack_rgba(float r, float g, float b) {
 }
 
 template <typename R>
-__device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R phi) {
+__device__ __forceinline__ void sky_rgb(unsigned long long seed, R theta, R phi, float rgb[3]) {
   int i = (int)m_floor(theta * R(5.09295817894065074));   // 16 / pi
   int j = (int)m_floor(phi * R(5.09295817894065074));     // 32 / (2 pi)
   i = min(15, max(0, i));
   j = min(31, max(0, j));
   const bool light = ((i + j) & 1) == 0;
   const unsigned long long hsh = splitmix64(seed * 2654435761ull + (unsigned long long)(32 * i + j));
-  float rgb[3];
   const float base[3] = {light ? 0.9f : 0.1f, light ? 0.9f : 0.1f, light ? 0.9f : 0.25f};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -659,8 +660,22 @@ __device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R
     // (0.75 + 0.25 slice / 2^24), evaluated in double-free single precision
     rgb[c] = base[c] * (0.75f + 0.25f * (slice * (1.0f / 16777216.0f)));
   }
+}
+
+template <typename R>
+__device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R phi) {
+  float rgb[3];
+  sky_rgb<R>(seed, theta, phi, rgb);
   return pack_rgba(rgb[0], rgb[1], rgb[2]);
 }
+
+// Colour accumulator of one pixel rendered with several samples: the
+// stratified samples add their linear colour; the extra ray through the
+// pixel centre stores the pixel's direction and flags.
+struct SppAcc {
+  float c[3];
+  bool centre;
+};
 
 template <typename R>
 __device__ __forceinline__ void dir_angles(R x, R y, R z, R* th, R* ph) {
@@ -684,18 +699,42 @@ __device__ __forceinline__ void store_ray(const Params& p, int out, OutR th, Out
   if (p.rgba) p.rgba[out] = rgba;
 }
 
+// Hand a finished ray's outputs over: stored directly, or with several
+// samples per pixel (SPP) added to the pixel's colour (stratified samples)
+// or stored without colour (the centre ray).
+template <typename OutR, bool SPP>
+__device__ __forceinline__ void emit_ray(const Params& p, int out, OutR th, OutR ph, unsigned flags,
+                                         const float c[3], SppAcc* acc) {
+  if (!SPP) {
+    store_ray<OutR>(p, out, th, ph, flags, pack_rgba(c[0], c[1], c[2]));
+  } else if (acc->centre) {
+    if (p.dirs) {
+      OutR* d = reinterpret_cast<OutR*>(p.dirs);
+      d[out] = th;
+      d[(long long)p.n_rays + out] = ph;
+    }
+    if (p.flags) p.flags[out] = (uint16_t)flags;
+  } else {
+    acc->c[0] += c[0];
+    acc->c[1] += c[1];
+    acc->c[2] += c[2];
+  }
+}
+
 // Map a terminated ray back to 3-D, shade it and store it.  The map-back
 // and shading run in the output precision OutR: an FP64 ray of the MIXED
 // band is reduced to phi mod 2 pi in FP64 and finished in FP32, as its
 // directions are stored in FP32.
-template <typename R, typename OutR>
-__device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) {
+template <typename R, typename OutR, bool SPP = false>
+__device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit,
+                           SppAcc* acc = nullptr) {
   using T = OutR;
   const SceneK& s = p.s;
   const unsigned fl = hit.flags & 0xFFu;
   const unsigned flags = hit.flags | (r.aux & 0xFFu);
+  float c[3] = {0.0f, 0.0f, 0.0f};
   if (fl == BH_FLAG_CAPT || fl == BH_FLAG_STEP_LIMIT) {
-    store_ray<OutR>(p, r.out, OutR(NAN), OutR(NAN), flags, 255u << 24);
+    emit_ray<OutR, SPP>(p, r.out, OutR(NAN), OutR(NAN), flags, c, acc);
     return;
   }
   R phr = hit.phi;
@@ -709,14 +748,15 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) 
   const T dz = cp * e1z + sp * e2z;
   T th, ph;
   dir_angles(dx, dy, dz, &th, &ph);
-  unsigned rgba;
   if (fl == BH_FLAG_ESC) {
-    rgba = sky_rgba<T>(s.seed, th, ph);
+    sky_rgb<T>(s.seed, th, ph, c);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
     const float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
     const float k = fmaf(0.7f, t, 0.3f);
-    rgba = pack_rgba(k, fmaf(0.65f, t, 0.35f) * k, fmaf(0.9f * t, t, 0.1f) * k);
+    c[0] = k;
+    c[1] = fmaf(0.65f, t, 0.35f) * k;
+    c[2] = fmaf(0.9f * t, t, 0.1f) * k;
   } else {  // sphere
     const int id = (int)(hit.flags >> 8);
     const T u = T(hit.u), v = T(hit.v);
@@ -731,9 +771,11 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit) 
             N2 = (dz * iu - S.c[id][2]) * iR;
     const float ndt = (float)(-(N0 * T0 + N1 * T1 + N2 * T2) * it);
     const float lam = 0.25f + 0.75f * fmaxf(0.0f, ndt);
-    rgba = pack_rgba(s.alb[id][0] * lam, s.alb[id][1] * lam, s.alb[id][2] * lam);
+    c[0] = s.alb[id][0] * lam;
+    c[1] = s.alb[id][1] * lam;
+    c[2] = s.alb[id][2] * lam;
   }
-  store_ray<OutR>(p, r.out, th, ph, flags, rgba);
+  emit_ray<OutR, SPP>(p, r.out, th, ph, flags, c, acc);
 }
 
 }  // namespace bhk

@@ -557,3 +557,34 @@ def polyline_escape_order(lib):
 
 
 POLYLINE = [polyline_straight_m0, polyline_nodes, polyline_escape_order]
+
+
+# --- anti-aliased pixels (n x n stratified samples, box filter) ---------
+
+def spp_mean(lib):
+    """A pixel rendered with n x n samples has, to one quantisation level,
+    the mean colour of rays traced separately through the centres of an
+    n x n grid over the pixel, and the centre ray's direction and flags."""
+    w = W.config2(32, "fp64")
+    cam = w.cameras[0]
+    n = 3
+    got = oracle.render(w.scene, w.cameras, oracle.opts(spp_n=n), lib=lib)
+    one = oracle.render(w.scene, w.cameras, oracle.opts(), lib=lib)
+    if not (np.array_equal(got["flags"], one["flags"])
+            and np.array_equal(got["theta"], one["theta"], equal_nan=True)):
+        return False, "directions or flags differ from the centre ray's"
+    bad = mixed = 0
+    for idx in range(0, cam.w * cam.h, 3):
+        x, y = idx % cam.w, idx // cam.w
+        cols = []
+        for j in range(n):
+            for i in range(n):
+                P, d = oracle.camera_ray(cam, x + (i + 0.5) / n - 0.5, y + (j + 0.5) / n - 0.5,
+                                         lib=lib)
+                rgba = int(oracle.render_world_ray(w.scene, P, d, lib=lib)["rgba"])
+                cols.append([(rgba >> (8 * c)) & 255 for c in range(3)])
+        cols = np.array(cols, float)
+        mixed += int(np.ptp(cols, axis=0).max() > 2)
+        px = np.array([(int(got["rgba"][idx]) >> (8 * c)) & 255 for c in range(3)])
+        bad += int(np.any(np.abs(px - cols.mean(axis=0)) > 1.0))
+    return bad == 0 and mixed > 10, f"{bad} pixels off the sample mean, {mixed} edge pixels"

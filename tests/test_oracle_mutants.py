@@ -53,6 +53,9 @@ MUTANTS = [
      "ev->phi_esc = phi + eps * un / (u - un);", [P.polyline_straight_m0, P.polyline_escape_order]),
     ("segment_plane_parameter", "double s = za / (za - zb), X[3];", "double s = zb / (za - zb), X[3];",
      [P.polyline_straight_m0, P.polyline_nodes]),
+    # anti-aliased pixels
+    ("spp_grid_offset", "double sx = x + (i + 0.5) / n - 0.5, sy = y + (j + 0.5) / n - 0.5;",
+     "double sx = x + (i + 0.0) / n - 0.5, sy = y + (j + 0.0) / n - 0.5;", [P.spp_mean]),
 ]
 
 
