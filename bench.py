@@ -293,7 +293,7 @@ def run_ours(args) -> None:
     rgba = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band,
-                          paper_eps=args.paper_eps, spp=args.spp)
+                          paper_eps=args.paper_eps, spp=args.spp, doppler=int(args.doppler))
     # rays traced per pixel: n x n samples plus the centre ray when anti-aliased
     rays_per_pixel = args.spp + 1 if args.spp > 1 else 1
 
@@ -422,6 +422,7 @@ def run_ours(args) -> None:
                    "band": w.band, "stated_exit_dir_error_rad": STATED_ERROR[args.form],
                    "paper_eps": args.paper_eps if paper else None,
                    "spp": args.spp if args.spp > 1 else None,
+                   "disk_shading": "keplerian doppler" if args.doppler else "temperature ramp",
                    "mpixels_per_s": job_rate(n, args.steps, world, ms * 1e-3),
                    "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps (outside the events)",
@@ -459,6 +460,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate", "paper", "paper_fp32"),
                     default="mixed")
+    ap.add_argument("--doppler", action="store_true",
+                    help="Keplerian disk with Doppler and gravitational shift")
     ap.add_argument("--spp", type=int, default=1,
                     help="samples per pixel (a square; fp32 and fp64 forms)")
     ap.add_argument("--paper-eps", type=float, default=0.01,

@@ -159,6 +159,13 @@ typedef struct bh_render_opts {
                          the pixel centre gives its direction and flags.
                          BH_MODE_FP32 and BH_MODE_FP64 only (else
                          BH_E_UNSUPPORTED); n <= 16                          */
+  int doppler;        /* 1: shade the disk as gas on prograde Keplerian orbits
+                         about +z, seen by the static camera: frequency ratio
+                         g = sqrt(1 - 3M/r) / (sqrt(1 - 2M/r_obs)(1 + Omega b
+                         n_z)), Omega = sqrt(M/r^3), b n_z the traced ray's
+                         angular momentum about z; the colour ramp is taken
+                         at g t and scaled by g^3 (g = 0 inside 3M).  The
+                         integrator modes only (else BH_E_UNSUPPORTED)      */
 } bh_render_opts;
 
 typedef struct bh_stats {

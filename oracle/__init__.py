@@ -61,7 +61,7 @@ class _Opts(ctypes.Structure):
                 ("phi_max", ctypes.c_double), ("max_steps", ctypes.c_long),
                 ("eps_r", ctypes.c_double), ("eps_ang", ctypes.c_double),
                 ("eps_b", ctypes.c_double), ("method", ctypes.c_int), ("eps", ctypes.c_double),
-                ("spp_n", ctypes.c_int)]
+                ("spp_n", ctypes.c_int), ("doppler", ctypes.c_int)]
 
 
 METHOD_DP5 = 0
@@ -113,6 +113,8 @@ def load(path: str = LIB) -> ctypes.CDLL:
         lib.or_splitmix64.argtypes = [ctypes.c_uint64]
         lib.or_threads.restype = ctypes.c_int
         lib.or_threads.argtypes = [ctypes.c_int]
+        lib.or_disk_g.restype = ctypes.c_double
+        lib.or_disk_g.argtypes = [ctypes.c_double, ctypes.c_double, _VP, _VP, ctypes.c_double]
         _libs[path] = lib
         return lib
 
@@ -147,11 +149,14 @@ def _cams(cams) -> ctypes.Array:
 
 
 def opts(rtol=1e-10, atol=1e-10, phi_max=64.0, max_steps=100000,
-         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6, method=METHOD_DP5, eps=0.01, spp_n=1) -> _Opts:
+         eps_r=1e-7, eps_ang=1e-9, eps_b=1e-6, method=METHOD_DP5, eps=0.01, spp_n=1,
+         doppler=0) -> _Opts:
     """Integration tolerances, caps and ambiguity thresholds; method 1 is the
     paper's fixed-step polyline with step eps (Sec. 2.1-2.2); spp_n > 1
-    averages n x n stratified samples per pixel into its colour."""
-    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b, method, eps, spp_n)
+    averages n x n stratified samples per pixel into its colour; doppler = 1
+    shades the disk as Keplerian gas with its Doppler and gravitational shift."""
+    return _Opts(rtol, atol, phi_max, max_steps, eps_r, eps_ang, eps_b, method, eps, spp_n,
+                 doppler)
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -278,3 +283,12 @@ def splitmix64(x: int, lib=None) -> int:
 def threads(n: int = 0, lib=None) -> int:
     lib = lib or load()
     return int(lib.or_threads(n))
+
+
+def disk_g(M: float, r_obs: float, x, t, dr_dphi: float, lib=None) -> float:
+    """Frequency ratio camera / emitter of the Keplerian disk at point x for
+    a traced ray with in-plane unit tangent t and dr/dphi there."""
+    lib = lib or load()
+    x = np.ascontiguousarray(x, np.float64)
+    t = np.ascontiguousarray(t, np.float64)
+    return float(lib.or_disk_g(M, r_obs, _ptr(x), _ptr(t), dr_dphi))

@@ -86,6 +86,7 @@ typedef struct {
                   fixed-step polyline (Sec. 2.1-2.2) */
   double eps;  /* step in phi of method 1 */
   int spp_n;   /* samples per pixel side: n x n stratified samples (<= 1: one) */
+  int doppler; /* 1: Keplerian disk with Doppler and gravitational shift */
 } or_opts;
 
 typedef struct {
@@ -640,6 +641,47 @@ static void disk_rgb(const or_scene *sc, double r, double rgb[3]) {
   rgb[2] = (0.1 + 0.9 * t * t) * k;
 }
 
+/* Keplerian disk seen by the static camera at r_obs: the frequency ratio
+ * g = nu_camera / nu_emitted of a photon reaching the camera from the disk
+ * point x (r = |x|, in the equatorial plane).  Worked in the local static
+ * frame at x: the gas moves on a prograde circular orbit (about +z) with
+ * speed beta = sqrt(M / (r - 2M)); the photon arrives along the unit vector
+ * kin, minus the traced ray's direction; with local frame components
+ * (radial scaled by 1/sqrt(1 - 2M/r)), the emitted energy in the static
+ * frame is gamma (1 - beta kin.phi_hat) times the gas frame's, and static
+ * energies at r and r_obs differ by sqrt(1 - 2M/r) / sqrt(1 - 2M/r_obs).
+ * Inside r = 3M there is no circular orbit: g = 0. */
+static double disk_g(double M, double r_obs, const double x[3], const double xr_dir[3],
+                     double dr_dphi, const double t_dir[3], double r) {
+  if (!(r > 3.0 * M)) return 0.0;
+  double f = 1.0 - 2.0 * M / r;
+  /* traced direction in the local orthonormal static frame: radial part
+   * (dr/dphi) / sqrt(f), tangential part r (per unit dphi) */
+  double kr = dr_dphi / sqrt(f), kt = r;
+  double nk = sqrt(kr * kr + kt * kt);
+  double kin[3];
+  for (int k = 0; k < 3; ++k) kin[k] = -(kr * xr_dir[k] + kt * t_dir[k]) / nk;
+  /* prograde azimuthal direction about +z at x */
+  double ph[3] = {-x[1], x[0], 0.0};
+  double nph = norm3(ph);
+  for (int k = 0; k < 3; ++k) ph[k] /= nph;
+  double beta = sqrt(M / (r - 2.0 * M));
+  double gamma = 1.0 / sqrt(1.0 - beta * beta);
+  double e_static_over_gas = 1.0 / (gamma * (1.0 - beta * dot3(kin, ph)));
+  return e_static_over_gas * sqrt(f) / sqrt(1.0 - 2.0 * M / r_obs);
+}
+
+/* Disk colour with the Keplerian shift g: the ramp at the observed
+ * temperature factor g t, brightness scaled by g^3. */
+static void disk_rgb_doppler(const or_scene *sc, double r, double g, double rgb[3]) {
+  double t = g * pow(sc->disk_r_in / r, 0.75);
+  double k = 0.3 + 0.7 * t;
+  double s = g * g * g;
+  rgb[0] = 1.0 * k * s;
+  rgb[1] = (0.35 + 0.65 * t) * k * s;
+  rgb[2] = (0.1 + 0.9 * t * t) * k * s;
+}
+
 /* ------------------------------------------------------------------ */
 /* The paper's own stepping (Sec. 2.1-2.2, Fig. 1): points of the ray at   */
 /* fixed steps eps in phi, computed with the classical fourth-order        */
@@ -883,7 +925,17 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
     sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
     if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
   } else if (ev.flags == OR_DISK) {
-    disk_rgb(sc, 1.0 / ev.u_evt, out->rgb);
+    if (o->doppler) {
+      double u = ev.u_evt, r = 1.0 / u, x[3], tdir[3];
+      for (int k = 0; k < 3; ++k) {
+        x[k] = dirv[k] * r;
+        tdir[k] = -sp * pl.e1[k] + cp * pl.e2[k];
+      }
+      double g = disk_g(M, norm3(P), x, dirv, -ev.v_evt / (u * u), tdir, r);
+      disk_rgb_doppler(sc, r, g, out->rgb);
+    } else {
+      disk_rgb(sc, 1.0 / ev.u_evt, out->rgb);
+    }
   } else { /* sphere */
     const or_sphere *S = &sc->spheres[ev.sphere_id];
     double u = ev.u_evt, v = ev.v_evt;
@@ -1151,3 +1203,12 @@ void or_sky_rgb(uint64_t seed, double theta, double phi, double *rgb) {
 
 /* splitmix64 output for state x, for unit tests. */
 uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
+
+/* Frequency ratio of the Keplerian disk shading (see disk_g), exposed for
+ * the tests: disk point x (equatorial, r = |x|), traced direction per unit
+ * phi given by dr/dphi and the in-plane unit tangent t. */
+double or_disk_g(double M, double r_obs, const double *x, const double *t, double dr_dphi) {
+  double r = norm3(x), xr[3];
+  for (int k = 0; k < 3; ++k) xr[k] = x[k] / r;
+  return disk_g(M, r_obs, x, xr, dr_dphi, t, r);
+}

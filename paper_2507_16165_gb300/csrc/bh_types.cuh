@@ -133,6 +133,7 @@ struct Params {
   double h_max_far;             // FP32 step cap of rays with |b - b_c| >= kFarB
   double paper_eps;             // fixed step of the polyline modes
   int spp_n;                    // samples per pixel side (n x n), 1 = one centre ray
+  int doppler;                  // Keplerian disk shading
   int max_steps;
   int peri_reset;
   unsigned long long abort_after;  // stop grabbing work past this slot (0 = off)

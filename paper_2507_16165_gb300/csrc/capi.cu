@@ -243,6 +243,9 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
     if (opts->mode != BH_MODE_FP32 && opts->mode != BH_MODE_FP64)
       return bh_fail(BH_E_UNSUPPORTED, "bh_render: spp > 1 needs BH_MODE_FP32 or BH_MODE_FP64");
   }
+  if (opts->doppler && opts->mode != BH_MODE_FP32 && opts->mode != BH_MODE_FP64 &&
+      opts->mode != BH_MODE_MIXED)
+    return bh_fail(BH_E_UNSUPPORTED, "bh_render: doppler shading needs an integrator mode");
   return BH_OK;
 }
 
@@ -294,6 +297,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
   c.paper_eps = o->paper_eps > 0 ? o->paper_eps : 0.01;
+  c.doppler = o->doppler ? 1 : 0;
   c.spp_n = 1;
   while (c.spp_n * c.spp_n < o->spp) ++c.spp_n;
   const TunedShape t = tuned_shape(sc, o->mode);
@@ -405,6 +409,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.h_max_far = cfg.h_max_far;
   p.paper_eps = cfg.paper_eps;
   p.spp_n = cfg.spp_n;
+  p.doppler = cfg.doppler;
   p.max_steps = cfg.max_steps;
   p.peri_reset = cfg.peri_reset;
   p.abort_after = cfg.abort_after;

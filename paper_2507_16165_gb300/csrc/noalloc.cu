@@ -116,8 +116,8 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
                    kNoAllocMaxCams, kNoAllocMaxCams);
   if (opts->mode != BH_MODE_FP32 && opts->mode != BH_MODE_FP64)
     return bh_fail(BH_E_UNSUPPORTED, "bh_render_noalloc: only BH_MODE_FP32 and BH_MODE_FP64");
-  if (opts->spp > 1)
-    return bh_fail(BH_E_UNSUPPORTED, "bh_render_noalloc: one sample per pixel only");
+  if (opts->spp > 1 || opts->doppler)
+    return bh_fail(BH_E_UNSUPPORTED, "bh_render_noalloc: one sample per pixel, plain disk shading only");
   if ((opts->tile_w || opts->tile_h) &&
       (opts->tile_w < 1 || opts->tile_h < 1 || opts->tile_w * opts->tile_h != 32))
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: tile_w * tile_h must be 32");

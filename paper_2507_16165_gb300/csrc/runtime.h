@@ -50,6 +50,7 @@ struct RenderConfig {
   int mode;
   double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, paper_eps;
   int spp_n;  // samples per pixel side
+  int doppler;
   int max_steps;
   int block, blocks_per_sm, tile_w, tile_h, budget;
   int band_lanes, band_warps;

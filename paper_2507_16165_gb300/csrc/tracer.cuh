@@ -699,6 +699,33 @@ __device__ __forceinline__ void store_ray(const Params& p, int out, OutR th, Out
   if (p.rgba) p.rgba[out] = rgba;
 }
 
+// Frequency ratio camera / gas of a disk hit for gas on prograde Keplerian
+// orbits about +z: with Omega = sqrt(M/r^3) and lambda = b n_z, the traced
+// ray's angular momentum about z per unit energy (the photon's is -lambda),
+//   g = sqrt(1 - 3M/r) / (sqrt(1 - 2M/r_obs) (1 + Omega lambda));
+// b from the first integral at the hit, 1/b^2 = u'^2 + u^2 (1 - 2Mu), and
+// r_obs from the camera the output pixel belongs to.  No circular orbit
+// inside 3M: g = 0.
+template <typename R>
+__device__ float disk_shift(const Params& p, const Ray<R>& r, float u, float v) {
+  const float M = p.s.f.M;
+  const float a = fmaf(-3.0f * M, u, 1.0f);
+  if (!(a > 0.0f)) return 0.0f;
+  int lo = 0, hi = p.n_cams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.cams[mid].out_off <= r.out)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const float u0 = p.cams[lo].f.ir;
+  const float b = rsqrt_approx(fmaf(v, v, u * u * fmaf(-2.0f * M, u, 1.0f)));
+  const float nz = (float)(r.e1x * r.e2y - r.e1y * r.e2x);
+  const float omega = sqrtf(M * u * u * u);
+  return sqrtf(a) * rsqrt_approx(fmaf(-2.0f * M, u0, 1.0f)) * rcp_approx(fmaf(omega * b, nz, 1.0f));
+}
+
 // Hand a finished ray's outputs over: stored directly, or with several
 // samples per pixel (SPP) added to the pixel's colour (stratified samples)
 // or stored without colour (the centre ray).
@@ -752,8 +779,14 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit,
     sky_rgb<T>(s.seed, th, ph, c);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
-    const float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
-    const float k = fmaf(0.7f, t, 0.3f);
+    float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
+    float bright = 1.0f;
+    if (p.doppler) {
+      const float g = disk_shift(p, r, (float)hit.u, (float)hit.v);
+      t *= g;
+      bright = g * g * g;
+    }
+    const float k = fmaf(0.7f, t, 0.3f) * bright;
     c[0] = k;
     c[1] = fmaf(0.65f, t, 0.35f) * k;
     c[2] = fmaf(0.9f * t, t, 0.1f) * k;

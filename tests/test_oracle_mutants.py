@@ -53,6 +53,11 @@ MUTANTS = [
      "ev->phi_esc = phi + eps * un / (u - un);", [P.polyline_straight_m0, P.polyline_escape_order]),
     ("segment_plane_parameter", "double s = za / (za - zb), X[3];", "double s = zb / (za - zb), X[3];",
      [P.polyline_straight_m0, P.polyline_nodes]),
+    # Keplerian disk shading
+    ("kepler_newtonian_speed", "double beta = sqrt(M / (r - 2.0 * M));", "double beta = sqrt(M / r);",
+     [P.doppler_closed_form]),
+    ("doppler_direction_sign", "kin[k] = -(kr * xr_dir[k] + kt * t_dir[k]) / nk;",
+     "kin[k] = (kr * xr_dir[k] + kt * t_dir[k]) / nk;", [P.doppler_closed_form]),
     # anti-aliased pixels
     ("spp_grid_offset", "double sx = x + (i + 0.5) / n - 0.5, sy = y + (j + 0.5) / n - 0.5;",
      "double sx = x + (i + 0.0) / n - 0.5, sy = y + (j + 0.0) / n - 0.5;", [P.spp_mean]),
