@@ -280,6 +280,9 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
 
     w = workload(args.form, args.size, args.workload)
+    if args.sky_image:
+        from dataclasses import replace
+        w = replace(w, scene=replace(w.scene, sky_texture=W.sky_texture(0, 2048, 1024)))
     n = w.n_rays
     sc = bh.Scene(w.scene)
     cams = sc.cameras(w.cameras)
@@ -423,6 +426,7 @@ def run_ours(args) -> None:
                    "paper_eps": args.paper_eps if paper else None,
                    "spp": args.spp if args.spp > 1 else None,
                    "disk_shading": "keplerian doppler" if args.doppler else "temperature ramp",
+                   "sky": "2048x1024 image, bilinear" if args.sky_image else "procedural checker",
                    "mpixels_per_s": job_rate(n, args.steps, world, ms * 1e-3),
                    "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps (outside the events)",
@@ -460,6 +464,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate", "paper", "paper_fp32"),
                     default="mixed")
+    ap.add_argument("--sky-image", action="store_true",
+                    help="a 2048x1024 synthetic sky image in place of the checker")
     ap.add_argument("--doppler", action="store_true",
                     help="Keplerian disk with Doppler and gravitational shift")
     ap.add_argument("--spp", type=int, default=1,

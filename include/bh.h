@@ -212,6 +212,18 @@ void bh_scene_destroy(bh_scene *scene);
 int bh_camera_set(bh_camera *cam, double r_obs, double incl_deg, double azim_deg,
                   double fov_deg);
 
+/* Use an image as the sky (the paper renders photographs as backgrounds,
+ * Sec. 3.1) in place of the procedural checker: texels is a host array of
+ * w x h RGBA8 values (red in the low byte), row-major, equirectangular --
+ * row j holds theta = (j + 1/2) pi / h measured from the +z pole, column i
+ * holds phi = (i + 1/2) 2 pi / w.  The colour in a direction is bilinear in
+ * linear colour between the four nearest texel centres, wrapping in phi and
+ * clamped at the first and last rows.  The library copies the image to the
+ * device (the caller keeps ownership of texels); texels = NULL restores the
+ * checker.  Synchronises the device.  w <= 65536, h <= 32768.
+ * Errors: BH_E_INVALID, BH_E_CUDA. */
+int bh_scene_sky_texture(bh_scene *scene, const uint32_t *texels, int w, int h);
+
 /* Render n_cams cameras in one persistent launch sequence.
  *   cams[n_cams], w[n_cams], h[n_cams]: host arrays; w, h >= 1; the total
  *     ray count must stay below 2^31 - 1.

@@ -47,7 +47,8 @@ class _Scene(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("disk_enabled", ctypes.c_int),
                 ("disk_r_in", ctypes.c_double), ("disk_r_out", ctypes.c_double),
                 ("n_spheres", ctypes.c_int), ("spheres", _Sphere * MAX_SPHERES),
-                ("sky_seed", ctypes.c_uint64), ("ic", ctypes.c_int)]
+                ("sky_seed", ctypes.c_uint64), ("ic", ctypes.c_int),
+                ("sky_tex", ctypes.c_void_p), ("sky_w", ctypes.c_int), ("sky_h", ctypes.c_int)]
 
 
 class _Camera(ctypes.Structure):
@@ -136,6 +137,12 @@ def _scene(scene) -> _Scene:
         s.spheres[k].albedo[:] = [float(x) for x in sp.albedo]
     s.sky_seed = int(scene.sky_seed)
     s.ic = int(getattr(scene, "ic", 0))
+    tex = getattr(scene, "sky_texture", None)
+    if tex is not None:
+        tex = np.ascontiguousarray(tex, np.uint32)
+        s._tex = tex                     # keeps the texels alive with the struct
+        s.sky_tex = tex.ctypes.data
+        s.sky_h, s.sky_w = tex.shape
     return s
 
 

@@ -70,6 +70,11 @@ typedef struct {
   or_sphere spheres[OR_MAX_SPHERES];
   uint64_t sky_seed;
   int ic; /* 0 = static observer, 1 = Euclidean ("linear direction") */
+  /* optional sky image (Sec. 3.1 renders photographs as the background):
+   * equirectangular RGBA8, row j at theta = (j + 1/2) pi / h from the +z
+   * pole, column i at phi = (i + 1/2) 2 pi / w; NULL: procedural checker */
+  const uint32_t *sky_tex;
+  int sky_w, sky_h;
 } or_scene;
 
 typedef struct {
@@ -603,6 +608,31 @@ static void sky_rgb(uint64_t seed, double theta, double phi, double rgb[3]) {
   }
 }
 
+/* Background colour in direction (theta, phi): the sky image, bilinear in
+ * linear colour between the four nearest texel centres (wrapping in phi,
+ * clamped at the poles), or the procedural checker. */
+static void sky_colour(const or_scene *sc, double theta, double phi, double rgb[3]) {
+  if (!sc->sky_tex) {
+    sky_rgb(sc->sky_seed, theta, phi, rgb);
+    return;
+  }
+  int W = sc->sky_w, H = sc->sky_h;
+  double x = phi / (2.0 * OR_PI) * W - 0.5, y = theta / OR_PI * H - 0.5;
+  double fx0 = floor(x), fy0 = floor(y);
+  double fx = x - fx0, fy = y - fy0;
+  long i0 = (long)fx0, j0 = (long)fy0;
+  long ia = ((i0 % W) + W) % W, ib = (((i0 + 1) % W) + W) % W;
+  long ja = j0 < 0 ? 0 : (j0 > H - 1 ? H - 1 : j0);
+  long jb = j0 + 1 < 0 ? 0 : (j0 + 1 > H - 1 ? H - 1 : j0 + 1);
+  uint32_t t00 = sc->sky_tex[ja * W + ia], t10 = sc->sky_tex[ja * W + ib];
+  uint32_t t01 = sc->sky_tex[jb * W + ia], t11 = sc->sky_tex[jb * W + ib];
+  for (int c = 0; c < 3; ++c) {
+    double c00 = ((t00 >> (8 * c)) & 255) / 255.0, c10 = ((t10 >> (8 * c)) & 255) / 255.0;
+    double c01 = ((t01 >> (8 * c)) & 255) / 255.0, c11 = ((t11 >> (8 * c)) & 255) / 255.0;
+    rgb[c] = (1.0 - fy) * ((1.0 - fx) * c00 + fx * c10) + fy * ((1.0 - fx) * c01 + fx * c11);
+  }
+}
+
 static int near_cell_edge(double theta, double phi, double eps) {
   double ti = 16.0 * theta / OR_PI;
   double dt = fabs(ti - floor(ti + 0.5)) * OR_PI / 16.0;
@@ -820,8 +850,8 @@ static void shade_polyline(const or_scene *sc, const or_opts *o, const or_plane 
     double cp = cos(ev->phi_esc), sp = sin(ev->phi_esc);
     for (int k = 0; k < 3; ++k) dirv[k] = cp * pl->e1[k] + sp * pl->e2[k];
     dir_angles(dirv, &out->theta, &out->phi);
-    sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
-    if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
+    sky_colour(sc, out->theta, out->phi, out->rgb);
+    if (!sc->sky_tex && near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
     return;
   }
   double r = norm3(ev->x);
@@ -895,8 +925,8 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
     }
     out->flags = OR_ESC;
     dir_angles(d, &out->theta, &out->phi);
-    sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
-    if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
+    sky_colour(sc, out->theta, out->phi, out->rgb);
+    if (!sc->sky_tex && near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
     return;
   }
   if (sc->disk_enabled && pl.disk_in_plane) out->ambig |= OR_AMB_DEGEN;
@@ -922,8 +952,8 @@ static void render_ray(const or_scene *sc, const or_opts *o, const double P[3],
   for (int k = 0; k < 3; ++k) dirv[k] = cp * pl.e1[k] + sp * pl.e2[k];
   dir_angles(dirv, &out->theta, &out->phi);
   if (ev.flags == OR_ESC) {
-    sky_rgb(sc->sky_seed, out->theta, out->phi, out->rgb);
-    if (near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
+    sky_colour(sc, out->theta, out->phi, out->rgb);
+    if (!sc->sky_tex && near_cell_edge(out->theta, out->phi, o->eps_ang)) out->ambig |= OR_AMB_SKY;
   } else if (ev.flags == OR_DISK) {
     if (o->doppler) {
       double u = ev.u_evt, r = 1.0 / u, x[3], tdir[3];

@@ -23,6 +23,7 @@ from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # no
                     BHError, check)
 
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
+           "bh_scene_sky_texture",
            "bh_camera_set", "bh_render", "bh_render_host", "bh_scene_sync",
            "bh_render_stats", "bh_render_noalloc", "bh_graph_create", "bh_graph_launch",
            "bh_graph_destroy", "bh_autotune", "bh_autotune_reset", "bh_surrogate_labels",
@@ -58,6 +59,20 @@ def scene_desc(scene) -> _capi.bh_scene_desc:
     d.sky_seed = int(scene.sky_seed)
     d.ic = int(getattr(scene, "ic", 0))
     return d
+
+
+def bh_scene_sky_texture(scene: int, texels) -> None:
+    """Use an equirectangular RGBA8 image (h x w uint32 host array) as the
+    sky; None restores the procedural checker."""
+    import numpy as np
+    if texels is None:
+        check(_capi.lib().bh_scene_sky_texture(scene, None, 0, 0), "bh_scene_sky_texture")
+        return
+    t = np.ascontiguousarray(texels, np.uint32)
+    if t.ndim != 2:
+        raise ValueError("texels must be an h x w array")
+    check(_capi.lib().bh_scene_sky_texture(scene, t.ctypes.data, t.shape[1], t.shape[0]),
+          "bh_scene_sky_texture")
 
 
 def bh_scene_create(desc: _capi.bh_scene_desc) -> int:
@@ -318,6 +333,9 @@ class Scene:
     def __init__(self, scene):
         self.spec = scene
         self.handle = bh_scene_create(scene_desc(scene))
+        tex = getattr(scene, "sky_texture", None)
+        if tex is not None:
+            bh_scene_sky_texture(self.handle, tex)
 
     def close(self):
         if self.handle:

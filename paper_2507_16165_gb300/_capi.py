@@ -113,6 +113,7 @@ SIGNATURES = [
     ("bh_last_error", ctypes.c_char_p, []),
     ("bh_scene_create", _I, [ctypes.POINTER(bh_scene_desc), ctypes.POINTER(_P)]),
     ("bh_scene_destroy", None, [_P]),
+    ("bh_scene_sky_texture", _I, [_P, _P, _I, _I]),
     ("bh_camera_set", _I, [ctypes.POINTER(bh_camera), ctypes.c_double, ctypes.c_double,
                            ctypes.c_double, ctypes.c_double]),
     ("bh_render", _I, [_P, ctypes.POINTER(bh_camera), _I, _P, _P, _P, _P, _P,

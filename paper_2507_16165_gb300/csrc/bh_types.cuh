@@ -55,6 +55,8 @@ struct SceneK {
   float alb[kMaxSph][3];
   unsigned long long seed;
   int ic;
+  const uint32_t* sky_tex;  // equirectangular RGBA8 sky image, or null: checker
+  int sky_w, sky_h;
   SceneR<float> f;
   SceneR<double> d;
 };

@@ -145,6 +145,37 @@ extern "C" int bh_scene_create(const bh_scene_desc* desc, bh_scene** out) {
   return BH_OK;
 }
 
+extern "C" int bh_scene_sky_texture(bh_scene* sc, const uint32_t* texels, int w, int h) {
+  if (!sc) return bh_fail(BH_E_INVALID, "bh_scene_sky_texture: null scene");
+  DeviceGuard g(sc->device);
+  if (!texels) {
+    cudaDeviceSynchronize();
+    cudaFree(sc->d_sky);
+    sc->d_sky = nullptr;
+    sc->sk.sky_tex = nullptr;
+    sc->sk.sky_w = sc->sk.sky_h = 0;
+    return BH_OK;
+  }
+  if (w < 1 || h < 1 || w > 65536 || h > 32768)
+    return bh_fail(BH_E_INVALID, "bh_scene_sky_texture: size %dx%d out of range", w, h);
+  const size_t bytes = (size_t)w * h * sizeof(uint32_t);
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_scene_sky_texture: allocation");
+  e = cudaMemcpy(d, texels, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return bh_cuda_fail(e, "bh_scene_sky_texture: upload");
+  }
+  cudaDeviceSynchronize();  // no render may still read the old image
+  cudaFree(sc->d_sky);
+  sc->d_sky = d;
+  sc->sk.sky_tex = d;
+  sc->sk.sky_w = w;
+  sc->sk.sky_h = h;
+  return BH_OK;
+}
+
 extern "C" void bh_scene_destroy(bh_scene* sc) {
   if (!sc) return;
   {
@@ -157,6 +188,7 @@ extern "C" void bh_scene_destroy(bh_scene* sc) {
     cudaFree(sc->d_stage_dirs);
     cudaFree(sc->d_stage_flags);
     cudaFree(sc->d_stage_rgba);
+    cudaFree(sc->d_sky);
     for (int i = 0; i < 4; ++i)
       if (sc->ev[i]) cudaEventDestroy(sc->ev[i]);
     for (int i = 0; i < 2; ++i)

@@ -138,7 +138,10 @@ __device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d
     dir_angles(d[0], d[1], d[2], &th, &ph);
     flags = BH_FLAG_ESC | aux;
     float c[3];
-    sky_rgb<R>(s.seed, th, ph, c);
+    if (s.sky_tex)
+      sky_image_rgb<R>(s, th, ph, c);
+    else
+      sky_rgb<R>(s.seed, th, ph, c);
     emit_ray<OutR, SPP>(p, out, OutR(th), OutR(ph), flags, c, acc);
   }
   st.count_flag(flags);

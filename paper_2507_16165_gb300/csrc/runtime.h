@@ -43,6 +43,7 @@ struct bh_scene {
   bool timed = false;
   bool band_used = false;  // last render ran the side-stream band pass
   SurrogateState* surr = nullptr;
+  uint32_t* d_sky = nullptr;  // sky image texels (bh_scene_sky_texture)
 };
 
 // Resolved options of one render.

@@ -645,6 +645,29 @@ __device__ __forceinline__ unsigned pack_rgba(float r, float g, float b) {
   return quant8(r) | (quant8(g) << 8) | (quant8(b) << 16) | (255u << 24);
 }
 
+// Sky image: bilinear in linear colour between the four texel centres
+// around (theta, phi), wrapping in phi, clamped at the first and last rows.
+template <typename R>
+__device__ __noinline__ void sky_image_rgb(const SceneK& s, R theta, R phi, float rgb[3]) {
+  const int W = s.sky_w, H = s.sky_h;
+  const R x = phi * R(W * 0.15915494309189535) - R(0.5);
+  const R y = theta * R(H * 0.31830988618379067) - R(0.5);
+  const R x0 = m_floor(x), y0 = m_floor(y);
+  const float fx = (float)(x - x0), fy = (float)(y - y0);
+  const int i0 = (int)x0, j0 = (int)y0;
+  const int ia = ((i0 % W) + W) % W, ib = (((i0 + 1) % W) + W) % W;
+  const int ja = min(H - 1, max(0, j0)), jb = min(H - 1, max(0, j0 + 1));
+  const uint32_t t00 = __ldg(&s.sky_tex[(size_t)ja * W + ia]), t10 = __ldg(&s.sky_tex[(size_t)ja * W + ib]);
+  const uint32_t t01 = __ldg(&s.sky_tex[(size_t)jb * W + ia]), t11 = __ldg(&s.sky_tex[(size_t)jb * W + ib]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float c00 = (float)((t00 >> (8 * c)) & 255u), c10 = (float)((t10 >> (8 * c)) & 255u);
+    const float c01 = (float)((t01 >> (8 * c)) & 255u), c11 = (float)((t11 >> (8 * c)) & 255u);
+    const float top = fmaf(fx, c10 - c00, c00), bot = fmaf(fx, c11 - c01, c01);
+    rgb[c] = fmaf(fy, bot - top, top) * (1.0f / 255.0f);
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void sky_rgb(unsigned long long seed, R theta, R phi, float rgb[3]) {
   int i = (int)m_floor(theta * R(5.09295817894065074));   // 16 / pi
@@ -776,7 +799,10 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit,
   T th, ph;
   dir_angles(dx, dy, dz, &th, &ph);
   if (fl == BH_FLAG_ESC) {
-    sky_rgb<T>(s.seed, th, ph, c);
+    if (s.sky_tex)
+      sky_image_rgb<T>(s, th, ph, c);
+    else
+      sky_rgb<T>(s.seed, th, ph, c);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
     float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));

@@ -48,6 +48,8 @@ class Scene:
     spheres: tuple = ()
     sky_seed: int = 0
     ic: int = 0                        # 0 static observer, 1 Euclidean
+    # optional equirectangular RGBA8 sky image (h x w uint32), None: checker
+    sky_texture: object = field(default=None, compare=False, hash=False)
 
 
 @dataclass(frozen=True)
@@ -171,3 +173,27 @@ def surrogate_samples(n: int, seed: int = 0, b_lo: float = 3.0 * math.sqrt(3.0) 
     r = rng.uniform(r_range[0], r_range[1], n)
     psi = math.pi - rng.uniform(0.0, math.pi, n)     # (0, pi]
     return np.exp(lb), r, psi
+
+
+def sky_texture(seed: int = 0, w: int = 512, h: int = 256):
+    """A synthetic equirectangular RGBA8 sky image (h x w, uint32), standing
+    in for the paper's background photographs: a smooth seeded colour field
+    (a few random low-order waves in theta and phi) with a sprinkling of
+    bright one-texel stars."""
+    import numpy as np
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    th = (np.arange(h) + 0.5) / h * math.pi
+    ph = (np.arange(w) + 0.5) / w * 2 * math.pi
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    img = np.zeros((h, w, 3))
+    for c in range(3):
+        acc = np.full((h, w), 0.35)
+        for _ in range(4):
+            k, m = rng.integers(1, 6), rng.integers(1, 6)
+            acc += rng.uniform(0.05, 0.15) * np.sin(k * T + rng.uniform(0, 6.3)) * \
+                np.cos(m * P + rng.uniform(0, 6.3))
+        img[..., c] = acc
+    stars = rng.random((h, w)) < 0.004
+    img[stars] = 1.0
+    q = np.clip(np.floor(img * 255 + 0.5), 0, 255).astype(np.uint32)
+    return q[..., 0] | (q[..., 1] << 8) | (q[..., 2] << 16) | (np.uint32(255) << 24)

@@ -650,3 +650,42 @@ def doppler_approaching_side_bluer(lib):
 
 
 DOPPLER = [doppler_closed_form, doppler_approaching_side_bluer]
+
+
+# --- image sky (equirectangular texture, bilinear) -----------------------
+
+def sky_texture_affine(lib):
+    """Bilinear interpolation reproduces affine functions exactly: with a
+    sky image whose red level is 20 + i and green 30 + 2 j at texel (i, j),
+    every escaping ray away from the phi seam and the pole rows has red
+    20 + x and green 30 + 2 y, x = phi w / 2 pi - 1/2, y = theta h / pi - 1/2,
+    to the quantisation step; a texel-centre direction returns its texel."""
+    from dataclasses import replace
+    import numpy as np
+    w_, h_ = 96, 48
+    i = np.arange(w_)[None, :].repeat(h_, 0)
+    j = np.arange(h_)[:, None].repeat(w_, 1)
+    tex = (20 + i) | ((30 + 2 * j) << 8) | (100 << 16) | (255 << 24)
+    tex = tex.astype(np.uint32)
+    base = W.config1(40)
+    scene = replace(base.scene, mass=0.0, sky_texture=tex)
+    cam = replace(base.cameras[0], fov_deg=120.0)
+    got = oracle.render(scene, [cam], oracle.opts(), lib=lib)
+    esc = (got["flags"] & 0xFF) == oracle.ESC
+    x = got["phi"][esc] / (2 * math.pi) * w_ - 0.5
+    y = got["theta"][esc] / math.pi * h_ - 0.5
+    inner = (x > 0.5) & (x < w_ - 1.5) & (y > 0.5) & (y < h_ - 1.5)
+    red = (got["rgba"][esc] & 255).astype(float)
+    green = ((got["rgba"][esc] >> 8) & 255).astype(float)
+    err = max(float(np.max(np.abs(red[inner] - (20 + x[inner])))),
+              float(np.max(np.abs(green[inner] - (30 + 2 * y[inner])))))
+    # texel centre: direction of texel (i, j) = (7, 11)
+    th, ph = (11 + 0.5) / h_ * math.pi, (7 + 0.5) / w_ * 2 * math.pi
+    d = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    one = oracle.render_world_ray(scene, -100.0 * d, d, lib=lib)   # straight through the hole
+    centre_ok = int(one["rgba"]) == int(tex[11, 7])
+    return inner.sum() > 500 and err <= 0.5 + 1e-9 and centre_ok, \
+        f"{int(inner.sum())} rays, max level error {err:.3f}, centre texel {'ok' if centre_ok else 'wrong'}"
+
+
+SKY_TEXTURE = [sky_texture_affine]

@@ -58,6 +58,12 @@ MUTANTS = [
      [P.doppler_closed_form]),
     ("doppler_direction_sign", "kin[k] = -(kr * xr_dir[k] + kt * t_dir[k]) / nk;",
      "kin[k] = (kr * xr_dir[k] + kt * t_dir[k]) / nk;", [P.doppler_closed_form]),
+    # image sky
+    ("sky_bilinear_weight", "rgb[c] = (1.0 - fy) * ((1.0 - fx) * c00 + fx * c10) + fy * ((1.0 - fx) * c01 + fx * c11);",
+     "rgb[c] = (1.0 - fy) * (fx * c00 + (1.0 - fx) * c10) + fy * ((1.0 - fx) * c01 + fx * c11);",
+     [P.sky_texture_affine]),
+    ("sky_texel_centre", "double x = phi / (2.0 * OR_PI) * W - 0.5, y = theta / OR_PI * H - 0.5;",
+     "double x = phi / (2.0 * OR_PI) * W, y = theta / OR_PI * H - 0.5;", [P.sky_texture_affine]),
     # anti-aliased pixels
     ("spp_grid_offset", "double sx = x + (i + 0.5) / n - 0.5, sy = y + (j + 0.5) / n - 0.5;",
      "double sx = x + (i + 0.0) / n - 0.5, sy = y + (j + 0.0) / n - 0.5;", [P.spp_mean]),
