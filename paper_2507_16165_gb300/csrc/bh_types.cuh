@@ -3,6 +3,8 @@
 
 #include <stdint.h>
 
+#include <cmath>
+
 #include "bh.h"
 
 namespace bhk {
@@ -76,7 +78,31 @@ struct CamK {
   // u0 part of the first integral, for the MIXED periastron solve
   double peri_k0;
   float peri_k0f;
+  // MIXED band as bounds on the squared image-plane radius (band_pixel)
+  float band_rho2_lo, band_rho2_hi;
+  int row_off;  // first row of this camera among all cameras' rows
 };
+
+// Fill a camera's MIXED band bounds: rays with |b - b_c| < band are those
+// whose image-plane radius rho = tan(alpha) satisfies rho^2 in (lo, hi),
+// from b(alpha) = r sin(alpha) / sqrt(1 - 2M/r) (static observer) or
+// r sin(alpha) / sqrt(1 - 2M sin^2(alpha) / r) (Euclidean), both increasing
+// in alpha.  band <= 0: an empty band.
+inline double band_rho2_of_b(double b, double r, double M, int ic) {
+  if (!(b > 0.0)) return 0.0;
+  double s = ic == 0 ? b * std::sqrt(1.0 - 2.0 * M / r) / r : b / std::sqrt(r * r + 2.0 * M * b * b / r);
+  if (!(s < 1.0)) return INFINITY;
+  return s * s / (1.0 - s * s);
+}
+inline void fill_cam_band(CamK& c, double M, int ic, double band) {
+  const double bc = 3.0 * std::sqrt(3.0) * M;
+  if (!(band > 0.0) || !(M > 0.0)) {
+    c.band_rho2_lo = c.band_rho2_hi = -1.0f;
+    return;
+  }
+  c.band_rho2_lo = (float)band_rho2_of_b(bc - band, c.r_obs, M, ic);
+  c.band_rho2_hi = (float)band_rho2_of_b(bc + band, c.r_obs, M, ic);
+}
 
 // Fill the periastron constant of a camera (after fill_cam_r).
 inline void fill_cam_peri(CamK& c, float M) {
@@ -145,7 +171,6 @@ struct Params {
   WorkK* ws;
   void* spill;        // Spill<R>[n_queue]
   int* band_list;     // queue slots deferred to FP64 [n_queue]
-  unsigned* band_bits;  // one bit per queue slot: set when the slot is a band ray
   int band_lanes;       // lanes of a band-pass warp that take rays (1..32)
   // surrogate mode
   const uint2* mlp_frag;       // fragment-ordered BF16 weights (bhs::NFRAG)

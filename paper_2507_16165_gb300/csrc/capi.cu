@@ -196,7 +196,6 @@ extern "C" void bh_scene_destroy(bh_scene* sc) {
     if (sc->fork) cudaEventDestroy(sc->fork);
     if (sc->join) cudaEventDestroy(sc->join);
     if (sc->side) cudaStreamDestroy(sc->side);
-    cudaFree(sc->d_bits);
     surrogate_release(sc);
   }
   delete sc;
@@ -364,9 +363,16 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
   if (e == cudaSuccess) e = grow(&sc->d_band, &sc->band_cap, (size_t)n_queue);
   const size_t spill_bytes = (mode_is_fp64(cfg.mode) ? sizeof(Spill<double>) : sizeof(Spill<float>));
   if (e == cudaSuccess) e = grow(&sc->d_spill, &sc->spill_cap, (size_t)n_queue * spill_bytes);
-  if (e == cudaSuccess && cfg.mode == BH_MODE_MIXED)
-    e = grow(&sc->d_bits, &sc->bits_cap, (size_t)(n_queue / 32 + 1));
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: workspace allocation");
+  // MIXED band bounds per camera (k_band_list and band_pixel)
+  int rows = 0;
+  for (int i = 0; i < n_cams; ++i) {
+    CamK& c = sc->h_cams[i];
+    fill_cam_band(c, sc->sk.M, sc->sk.ic, cfg.mode == BH_MODE_MIXED || cfg.mode == BH_MODE_SURROGATE
+                                              ? cfg.band : 0.0);
+    c.row_off = rows;
+    rows += c.h;
+  }
   e = cudaMemcpyAsync(cams_dev, sc->h_cams.data(), n_cams * sizeof(CamK), cudaMemcpyHostToDevice,
                       upload_stream);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: camera upload");
@@ -374,8 +380,8 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
   fill_params(sc, cfg, n_cams, n_queue, n_rays, dirs, flags, rgba, &p);
   p.cams = cams_dev;
   LaunchShape ls{sc->num_sms, cfg.block, cfg.blocks_per_sm};
+  ls.band_rows = rows;
   if (cfg.mode == BH_MODE_MIXED) {
-    p.band_bits = sc->d_bits;
     ls.side = sc->side;
     ls.fork = sc->fork;
     ls.join = sc->join;

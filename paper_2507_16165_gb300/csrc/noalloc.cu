@@ -159,6 +159,8 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     fill_cam_r(c, &c.f);
     fill_cam_r(c, &c.d);
     fill_cam_peri(c, sk.f.M);
+    fill_cam_band(c, sk.M, sk.ic, 0.0);  // no band pass here
+    c.row_off = 0;
     q += 32LL * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }

@@ -184,16 +184,38 @@ __device__ __forceinline__ float periastron64(float M, double m2, float v0f, dou
   return fmaf(-(float)f, 1.0f / (u * fmaf(3.0f * m2f, u, -2.0f)), u);
 }
 
+// Photon-sphere band of the MIXED mode as a test on the pixel: a camera
+// looks at the hole, so the ray through image-plane point (sx, sy) makes the
+// angle alpha with tan(alpha) = rho = |(sx, sy)| with the direction of the
+// hole, and its impact parameter grows with alpha.  The band
+// |b - 3 sqrt(3) M| < band is then rho^2 in (band_rho2_lo, band_rho2_hi),
+// bounds the host derives per camera.  The list builder and the passes that
+// skip band rays evaluate this same function, so they agree on every pixel.
+__device__ __forceinline__ bool band_pixel(const CamK& c, int px, int py) {
+  const float sx = fmaf((float)px + 0.5f, c.f.px_scale, -c.f.sx);
+  const float sy = fmaf(-((float)py + 0.5f), c.f.py_scale, c.f.sy);
+  const float rho2 = fmaf(sx, sx, sy * sy);
+  return rho2 > c.band_rho2_lo && rho2 < c.band_rho2_hi;
+}
+
+// Queue slot of pixel (px, py) of camera c (the inverse of slot_pixel).
+__device__ __forceinline__ long long pixel_slot(const Params& p, const CamK& c, int px, int py) {
+  const int tx = px / p.tile_w, ty = py / p.tile_h;
+  const int i = (py - ty * p.tile_h) * p.tile_w + (px - tx * p.tile_w);
+  return c.q_off + ((long long)ty * c.tiles_x + tx) * 32 + i;
+}
+
 // Set up the ray of queue slot q.  Returns true when the ray is to be
 // integrated by the caller; false when it was padding, finished directly
 // (radial) or deferred to the FP64 band list.
 template <typename R, int MODE, typename OutR, bool SPP = false>
 __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out,
                            R ox = R(0.5), R oy = R(0.5), SppAcc* acc = nullptr) {
-  if (MODE == MODE_MIXED && p.band_bits && ((p.band_bits[q >> 5] >> (q & 31)) & 1u)) return false;
   int cam, px, py, out;
   if (!slot_pixel(p, q, &cam, &px, &py, &out)) return false;
   const CamK& c = p.cams[cam];
+  // band rays belong to the FP64 pass (listed by k_band_list)
+  if (MODE == MODE_MIXED && band_pixel(c, px, py)) return false;
   R P[3], d[3];
   camera_ray<R>(c, px, py, P, d, ox, oy);
   r.out = out;
@@ -206,14 +228,6 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   }
   *b_out = b;
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
-  if (MODE == MODE_MIXED && !p.band_bits) {
-    if (m_abs(b - SR<R>(p.s).b_crit) < tol.band) {
-      const unsigned long long k = atomicAdd(&p.ws->band_count, 1ull);
-      p.band_list[k] = (int)q;
-      st.c[ST_BAND]++;
-      return false;
-    }
-  }
   if (MODE == MODE_MIXED)
     r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
   r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), tol.phi_max);
@@ -228,45 +242,60 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   return true;
 }
 
-// Band pre-pass of the MIXED mode: one warp per 32-slot tile computes each
-// ray's impact parameter in FP32 and marks |b - 3 sqrt(3) M| < band in the
-// bitmap (one word per tile) and the FP64 band list (one atomic per warp).
-// The coherent pass then skips marked slots, so the two FP64 and FP32
-// passes can run at the same time.
-__global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Params p) {
+// Band list of the MIXED mode: one warp per image row finds the columns
+// where the row meets the band annulus (two x intervals from the bounds on
+// rho^2), its lanes test band_pixel on them and two pixels beyond each end,
+// and the warp appends the band rays' queue slots to the FP64 list with one
+// atomic per 32 columns.
+__global__ void __launch_bounds__(256) k_band_list(const __grid_constant__ Params p, int n_rows) {
   const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  const SceneR<float>& S = p.s.f;
-  const float bc = S.b_crit, band = p.tf.band, M = S.M;
+  const int warps = gridDim.x * (blockDim.x >> 5);
   LocalStats st;
   st.zero();
-  for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       t * 32 < p.n_queue; t += warps) {
-    const long long q = t * 32 + lane;
-    int cam, px, py, out;
-    bool in_band = false;
-    if (slot_pixel(p, q, &cam, &px, &py, &out)) {
-      const CamK& c = p.cams[cam];
-      float P[3], d[3];
-      camera_ray<float>(c, px, py, P, d);
-      const float r0 = c.f.r_obs, ir = 1.0f / r0;
-      const float c0 = P[1] * d[2] - P[2] * d[1], c1 = P[2] * d[0] - P[0] * d[2],
-                  c2 = P[0] * d[1] - P[1] * d[0];
-      const float sin_a = sqrtf(c0 * c0 + c1 * c1 + c2 * c2) * ir;
-      const float b = (p.s.ic == 0) ? r0 * sin_a * rsqrtf(1.0f - 2.0f * M * ir)
-                                    : r0 * sin_a * rsqrtf(1.0f - 2.0f * M * sin_a * sin_a * ir);
-      in_band = fabsf(b - bc) < band;
+  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n_rows; row += warps) {
+    int lo = 0, hi = p.n_cams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.cams[mid].row_off <= row)
+        lo = mid;
+      else
+        hi = mid - 1;
     }
-    const unsigned bits = __ballot_sync(kFull, in_band);
-    unsigned long long base = 0;
-    if (lane == 0) {
-      p.band_bits[t] = bits;
-      if (bits) base = atomicAdd(&p.ws->band_count, (unsigned long long)__popc(bits));
+    const CamK& c = p.cams[lo];
+    const int py = row - c.row_off;
+    if (!(c.band_rho2_hi > c.band_rho2_lo)) continue;
+    const float sy = fmaf(-((float)py + 0.5f), c.f.py_scale, c.f.sy);
+    const float out2 = c.band_rho2_hi - sy * sy;
+    if (!(out2 > 0.0f)) continue;
+    const float a = sqrtf(fmaxf(0.0f, c.band_rho2_lo - sy * sy)), bnd = sqrtf(out2);
+    // columns x with |sx| in (a, bnd), sx = (x + 1/2) px_scale - sx_half
+    const float ip = 1.0f / c.f.px_scale;
+    const float xl[2] = {(-bnd + c.f.sx) * ip - 0.5f, (a + c.f.sx) * ip - 0.5f};
+    const float xh[2] = {(-a + c.f.sx) * ip - 0.5f, (bnd + c.f.sx) * ip - 0.5f};
+    int from[2], to[2];
+    for (int k = 0; k < 2; ++k) {
+      from[k] = max(0, (int)floorf(xl[k]) - 2);
+      to[k] = min(c.w - 1, (int)ceilf(xh[k]) + 2);
     }
-    base = __shfl_sync(kFull, base, 0);
-    if (in_band) {
-      p.band_list[base + __popc(bits & ((1u << lane) - 1u))] = (int)q;
-      st.c[ST_BAND]++;
+    if (from[1] <= to[0] + 1) {  // the two intervals touch: one scan
+      to[0] = max(to[0], to[1]);
+      from[1] = 1;
+      to[1] = 0;
+    }
+    for (int k = 0; k < 2; ++k) {
+      for (int x0 = from[k]; x0 <= to[k]; x0 += 32) {
+        const int px = x0 + lane;
+        const bool in = px <= to[k] && band_pixel(c, px, py);
+        const unsigned bits = __ballot_sync(kFull, in);
+        if (!bits) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.ws->band_count, (unsigned long long)__popc(bits));
+        base = __shfl_sync(kFull, base, 0);
+        if (in) {
+          p.band_list[base + __popc(bits & ((1u << lane) - 1u))] = (int)pixel_slot(p, c, px, py);
+          st.c[ST_BAND]++;
+        }
+      }
     }
   }
   st.flush(p.ws);
@@ -998,7 +1027,8 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
-  } else if (!ls.side || !p.band_bits) {
+  } else if (!ls.side) {
+    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
     rec(1);
@@ -1011,9 +1041,9 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
     rec(3);
   } else {
-    // band pre-pass, then the FP64 band pass on the high-priority side
-    // stream concurrently with the FP32 coherent and long-ray passes
-    k_band_scan<<<ls.num_sms * 8, 256, 0, stream>>>(p);
+    // band list, then the FP64 band pass on the high-priority side stream
+    // concurrently with the FP32 coherent and long-ray passes
+    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
     cudaEventRecord(ls.fork, stream);
     cudaStreamWaitEvent(ls.side, ls.fork, 0);
     if (ls.band_ev && ls.band_ev[0]) record(ls.band_ev[0], ls.side);
@@ -1047,7 +1077,7 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
       cudaEventRecord(e, s);
   };
   if (ev) record(ev[0], stream);
-  k_band_scan<<<ls.num_sms * 8, 256, 0, stream>>>(p);
+  k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
   cudaEventRecord(ls.fork, stream);
   cudaStreamWaitEvent(ls.side, ls.fork, 0);
   if (ls.band_ev) record(ls.band_ev[0], ls.side);

@@ -17,6 +17,7 @@ struct LaunchShape {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t* band_ev = nullptr;
   int band_warps = 4;  // band-pass warps per SM (one-warp blocks)
+  int band_rows = 0;   // image rows over all cameras (band list threads)
 };
 
 // Launch the kernels of one render (coherent pass, long-ray pass and, in

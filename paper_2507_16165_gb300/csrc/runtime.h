@@ -38,8 +38,6 @@ struct bh_scene {
   cudaEvent_t band_ev[2] = {nullptr, nullptr};
   cudaStream_t side = nullptr;               // FP64 band pass (MIXED)
   cudaEvent_t fork = nullptr, join = nullptr;
-  unsigned* d_bits = nullptr;                // band bitmap, one bit per queue slot
-  size_t bits_cap = 0;
   bool timed = false;
   bool band_used = false;  // last render ran the side-stream band pass
   SurrogateState* surr = nullptr;

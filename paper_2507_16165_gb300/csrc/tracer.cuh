@@ -498,9 +498,12 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
   }
   // spheres cut by the plane
   unsigned mask = 0;
-  for (int k = 0; k < s.n_sph; ++k) {
-    const R sd = nx * S.c[k][0] + ny * S.c[k][1] + nz * S.c[k][2];
-    if (m_abs(sd) < S.rad[k]) mask |= 1u << k;
+#pragma unroll
+  for (int k = 0; k < kMaxSph; ++k) {
+    if (k < s.n_sph) {
+      const R sd = nx * S.c[k][0] + ny * S.c[k][1] + nz * S.c[k][2];
+      if (m_abs(sd) < S.rad[k]) mask |= 1u << k;
+    }
   }
   r.sph_mask = mask;
   r.phi_sph = R(INFINITY);
