@@ -183,9 +183,11 @@ typedef struct bh_stats {
   uint64_t steps_fp64;    /* attempted steps taken in FP64 (part of steps)   */
   uint32_t status;        /* BH_STATUS_* bits of the last render             */
   float kernel_ms[4];     /* device time of the last render: [0] coherent pass
-                             (with the MIXED band pre-pass), [1] long-ray pass,
-                             [2] FP64 band pass (MIXED; it overlaps [0] and [1]
-                             on a side stream), [3] whole render            */
+                             (MIXED: with the band list and the FP64 band
+                             pass, which runs beside it), [1] long-ray pass,
+                             [2] FP64 band pass of the surrogate mode (on a
+                             side stream beside [0] and [1]; 0 otherwise),
+                             [3] whole render                               */
 } bh_stats;
 
 /* Library version (BH_ABI_VERSION). */

@@ -24,11 +24,12 @@ TunedShape default_shape(int mode) {
   t.tile_w = 8;
   t.tile_h = 4;
   t.budget = (mode == BH_MODE_FP64) ? 256 : 48;
-  // MIXED: 128-thread blocks, six per SM, leave registers on every SM for
-  // the FP64 band pass that runs alongside
+  // MIXED: 128-thread blocks, eight per SM (the full register file at 64
+  // registers); seven fit beside the FP64 band pass's four warps per SM and
+  // the eighth starts as they leave
   if (mode == BH_MODE_MIXED) {
     t.block = 128;
-    t.blocks_per_sm = 6;
+    t.blocks_per_sm = 8;
   }
   t.band_lanes = 32;
   t.band_warps = 4;
@@ -62,9 +63,8 @@ extern "C" int bh_autotune(bh_scene* scene, const bh_camera* cams, int n_cams, c
   std::vector<TunedShape> cands;
   const int tiles[3][2] = {{8, 4}, {4, 8}, {16, 2}};
   const int budgets32[2] = {32, 64}, budgets64[2] = {128, 256};
-  // (block size, resident blocks per SM; 0 = as many as fit): MIXED keeps
-  // room for its concurrent band pass
-  const int res_mixed[3][2] = {{128, 6}, {128, 5}, {256, 3}};
+  // (block size, resident blocks per SM; 0 = as many as fit)
+  const int res_mixed[3][2] = {{128, 8}, {128, 7}, {256, 4}};
   const int res_other[2][2] = {{128, 0}, {256, 0}};
   const bool mixed = mode == BH_MODE_MIXED;
   const int n_res = mixed ? 3 : 2;

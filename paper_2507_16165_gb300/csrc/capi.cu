@@ -381,13 +381,7 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
   p.cams = cams_dev;
   LaunchShape ls{sc->num_sms, cfg.block, cfg.blocks_per_sm};
   ls.band_rows = rows;
-  if (cfg.mode == BH_MODE_MIXED) {
-    ls.side = sc->side;
-    ls.fork = sc->fork;
-    ls.join = sc->join;
-    ls.band_ev = sc->band_ev;
-    ls.band_warps = cfg.band_warps;
-  }
+  if (cfg.mode == BH_MODE_MIXED) ls.band_warps = cfg.band_warps;
   out->ls = ls;
   out->kmode = cfg.mode == BH_MODE_FP64             ? MODE_FP64
                : cfg.mode == BH_MODE_FP32           ? MODE_FP32
@@ -421,7 +415,7 @@ int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
   if (rc) return rc;
   sc->last_stream = stream;
   sc->timed = true;
-  sc->band_used = (pr.mode == BH_MODE_MIXED);
+  sc->band_used = false;
   return BH_OK;
 }
 

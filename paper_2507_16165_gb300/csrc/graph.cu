@@ -79,6 +79,6 @@ extern "C" int bh_graph_launch(bh_graph* g, void* stream) {
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_graph_launch");
   g->scene->last_stream = (cudaStream_t)stream;
   g->scene->timed = true;
-  g->scene->band_used = (g->mode == BH_MODE_MIXED);
+  g->scene->band_used = false;
   return BH_OK;
 }

@@ -7,7 +7,8 @@
 // like -ln|b - 3 sqrt(3) M| -- is saved to the long-ray list and finished by
 // a second persistent kernel whose lanes refill one ray at a time, so one
 // slow ray never holds 31 idle lanes.  In MIXED mode rays inside the band
-// |b - b_c| < band go to a third list that an FP64 kernel finishes.
+// |b - b_c| < band go to a third list that an FP64 kernel finishes beside
+// the FP32 coherent pass.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -362,17 +363,27 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
   Hermite<E> H;
   H.make(pa_e, E(h), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
   if (MODE == MODE_MIXED && peri) {
-    // periastron reset: truncate the step at the turning point and put the
-    // state back on the orbit of the initial conditions, (u_p, 0) with u_p
-    // from the FP64 cubic
+    // periastron reset: the step passed the turning point at pa + tp h;
+    // replace its end state by the point of the orbit through (u_p, 0) there
+    // (u_p from the FP64 cubic), so no FP32 drift of the incoming leg is
+    // carried into the outgoing one.  The orbit is even about the turning
+    // point (u' = u''' = u^(5) = 0 there), so with d = (1 - tp) h and
+    // F(u) = 3Mu^2 - u:  u = u_p + F d^2/2 + F' F d^4/24
+    // + (18M F^2 + F'^2 F) d^6/720, F and F' = 6Mu - 1 taken at u_p; the
+    // d^8 term is below 2e-8 u_p for d <= 0.4.  The step keeps its length.
     const E tp = turning_t<E>(H, M3);
     if (tp > E(0) && r.up == r.up) {
-      const R hp = R(tp) * h;
-      pb = pa + hp;
-      un = r.up;
-      vn = R(0);
-      fn = accel(SR<R>(s).M3, un);
-      H.make(pa_e, E(hp), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
+      const R M3r = SR<R>(s).M3;
+      const R d = (R(1) - R(tp)) * h, d2 = d * d;
+      const R F0 = accel(M3r, r.up);
+      const R F1 = m_fma(R(2) * M3r, r.up, R(-1));
+      const R c2 = R(0.5) * F0;
+      const R c4 = F1 * F0 * R(1.0 / 24.0);
+      const R c6 = m_fma(R(6) * M3r * F0, F0, F1 * F1 * F0) * R(1.0 / 720.0);
+      un = m_fma(d2, m_fma(d2, m_fma(d2, c6, c4), c2), r.up);
+      vn = d * m_fma(d2, m_fma(d2, R(6) * c6, R(4) * c4), R(2) * c2);
+      fn = accel(M3r, un);
+      H.make(pa_e, E(h), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
     }
     r.aux |= kAuxPeriDone;
     st.c[ST_PERI]++;
@@ -515,6 +526,105 @@ __device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool 
 // spill a few words but run 2% faster than at 80 with three blocks.
 template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
 
+// Re-create a ray from its queue slot and, for a long ray, its saved state.
+template <typename R, int MODE, typename OutR>
+__device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ray<R>& r,
+                            LocalStats& st) {
+  R b;
+  if (!setup_slot<R, MODE, OutR>(p, q, r, st, &b)) return false;
+  if (sp) {
+    r.steps = sp->steps;
+    r.aux = sp->aux;
+    r.u = sp->u;
+    r.v = sp->v;
+    r.phi = sp->phi;
+    r.h = sp->h;
+    r.f = accel(SR<R>(p.s).M3, r.u);
+    for (int it = 0; it < 64 && r.phi_node <= r.phi; ++it) r.phi_node += Num<R>::pi;
+    if (r.sph_mask) r.phi_sph = next_sphere_window<R>(r, r.phi);
+    r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), TolPick<R, MODE>::get(p).phi_max);
+  }
+  return true;
+}
+
+// Sources of the list-driven pass.
+enum { SRC_SPILL = 0, SRC_BAND = 1, SRC_SURR = 2 };
+
+// Long-ray pass: every lane refills on its own from a list (saved long
+// rays, FP64 band rays, or rays the surrogate sends back to the integrator),
+// warp-aggregated: one atomic per refill round.
+template <typename R, int MODE, typename OutR, int SRC>
+__device__ __forceinline__ void list_pass(const Params& p, LocalStats& st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  constexpr bool FROM_SPILL = SRC == SRC_SPILL;
+  unsigned long long* next = SRC == SRC_SPILL ? &p.ws->long_next
+                             : SRC == SRC_BAND ? &p.ws->band_next
+                                               : &p.ws->surr_next;
+  const unsigned long long total =
+      SRC == SRC_SPILL  ? *(volatile unsigned long long*)&p.ws->long_count
+      : SRC == SRC_BAND ? *(volatile unsigned long long*)&p.ws->band_count
+                        : *(volatile unsigned long long*)&p.ws->surr_count;
+  Ray<R> r;
+  bool active = false, exhausted = false;
+  for (long long guard = 0; guard < (1ll << 40); ++guard) {
+    if (!exhausted) {
+      const int lanes = SRC == SRC_BAND ? p.band_lanes : 32;
+      const unsigned need = __ballot_sync(kFull, !active && lane < lanes);
+      if (need) {
+        unsigned long long base = 0;
+        if (lane == 0) {
+          base = atomicAdd(next, (unsigned long long)__popc(need));
+          st.c[ST_GRABS]++;
+        }
+        base = __shfl_sync(kFull, base, 0);
+        if (base + __popc(need) >= total) exhausted = true;
+        if (!active) {
+          const unsigned long long idx = base + __popc(need & lt_mask);
+          if (idx < total) {
+            if (FROM_SPILL) {
+              const Spill<R> sp = reinterpret_cast<const Spill<R>*>(p.spill)[idx];
+              active = restore_ray<R, MODE, OutR>(p, sp.q, &sp, r, st);
+            } else {
+              const int* list = SRC == SRC_BAND ? p.band_list : p.surr_list;
+              active = restore_ray<R, MODE, OutR>(p, list[idx], nullptr, r, st);
+            }
+          }
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (active) {
+      Hit<R> hit;
+      if (advance<R, MODE>(p, r, hit, st)) {
+        finish_ray<R, OutR>(p, r, hit);
+        st.count_flag(hit.flags | r.aux);
+        active = false;
+      }
+    }
+  }
+}
+
+// The FP64 band pass is held to 64 registers, so one band warp and seven
+// 128-thread FP32 blocks fill an SM sub-partition's register file; it lets
+// the dependent coherent pass launch at once (see k_coherent).
+template <typename R, int MODE, typename OutR, int SRC>
+__global__ void __launch_bounds__(256, MODE == MODE_BAND64 ? 4 : kMinBlocks<R>)
+    k_longrays(const __grid_constant__ Params p) {
+  if (SRC == SRC_BAND) pdl_launch_dependents();
+  LocalStats st;
+  st.zero();
+  list_pass<R, MODE, OutR, SRC>(p, st);
+  st.flush(p.ws);
+}
+
+// In MIXED mode the pass is launched as a programmatic dependent of the
+// FP64 band pass, so its blocks fill the SMs beside the resident band warps
+// (and take the band warps' places as they leave); each block waits for the
+// band pass to complete before it exits, so the render ends after both.
 template <typename R, int MODE, typename OutR, bool SPP = false>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
   const int lane = threadIdx.x & 31;
@@ -564,91 +674,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
     }
   }
   st.flush(p.ws);
-}
-
-// Re-create a ray from its queue slot and, for a long ray, its saved state.
-template <typename R, int MODE, typename OutR>
-__device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ray<R>& r,
-                            LocalStats& st) {
-  R b;
-  if (!setup_slot<R, MODE, OutR>(p, q, r, st, &b)) return false;
-  if (sp) {
-    r.steps = sp->steps;
-    r.aux = sp->aux;
-    r.u = sp->u;
-    r.v = sp->v;
-    r.phi = sp->phi;
-    r.h = sp->h;
-    r.f = accel(SR<R>(p.s).M3, r.u);
-    for (int it = 0; it < 64 && r.phi_node <= r.phi; ++it) r.phi_node += Num<R>::pi;
-    if (r.sph_mask) r.phi_sph = next_sphere_window<R>(r, r.phi);
-    r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), TolPick<R, MODE>::get(p).phi_max);
-  }
-  return true;
-}
-
-// Sources of the list-driven pass.
-enum { SRC_SPILL = 0, SRC_BAND = 1, SRC_SURR = 2 };
-
-// Long-ray pass: every lane refills on its own from a list (saved long
-// rays, FP64 band rays, or rays the surrogate sends back to the integrator),
-// warp-aggregated: one atomic per refill round.
-template <typename R, int MODE, typename OutR, int SRC>
-__global__ void __launch_bounds__(256, kMinBlocks<R>) k_longrays(const __grid_constant__ Params p) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  constexpr bool FROM_SPILL = SRC == SRC_SPILL;
-  unsigned long long* next = SRC == SRC_SPILL ? &p.ws->long_next
-                             : SRC == SRC_BAND ? &p.ws->band_next
-                                               : &p.ws->surr_next;
-  const unsigned long long total =
-      SRC == SRC_SPILL  ? *(volatile unsigned long long*)&p.ws->long_count
-      : SRC == SRC_BAND ? *(volatile unsigned long long*)&p.ws->band_count
-                        : *(volatile unsigned long long*)&p.ws->surr_count;
-  LocalStats st;
-  st.zero();
-  Ray<R> r;
-  bool active = false, exhausted = false;
-  for (long long guard = 0; guard < (1ll << 40); ++guard) {
-    if (!exhausted) {
-      const int lanes = SRC == SRC_BAND ? p.band_lanes : 32;
-      const unsigned need = __ballot_sync(kFull, !active && lane < lanes);
-      if (need) {
-        unsigned long long base = 0;
-        if (lane == 0) {
-          base = atomicAdd(next, (unsigned long long)__popc(need));
-          st.c[ST_GRABS]++;
-        }
-        base = __shfl_sync(kFull, base, 0);
-        if (base + __popc(need) >= total) exhausted = true;
-        if (!active) {
-          const unsigned long long idx = base + __popc(need & lt_mask);
-          if (idx < total) {
-            if (FROM_SPILL) {
-              const Spill<R> sp = reinterpret_cast<const Spill<R>*>(p.spill)[idx];
-              active = restore_ray<R, MODE, OutR>(p, sp.q, &sp, r, st);
-            } else {
-              const int* list = SRC == SRC_BAND ? p.band_list : p.surr_list;
-              active = restore_ray<R, MODE, OutR>(p, list[idx], nullptr, r, st);
-            }
-          }
-        }
-      }
-    }
-    if (!__any_sync(kFull, active)) {
-      if (exhausted) break;
-      continue;
-    }
-    if (active) {
-      Hit<R> hit;
-      if (advance<R, MODE>(p, r, hit, st)) {
-        finish_ray<R, OutR>(p, r, hit);
-        st.count_flag(hit.flags | r.aux);
-        active = false;
-      }
-    }
-  }
-  st.flush(p.ws);
+  if (MODE == MODE_MIXED) pdl_wait_primary();
 }
 
 // Surrogate pass.  One 32-ray tile per warp grab: set up each ray as the
@@ -1027,37 +1053,29 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
-  } else if (!ls.side) {
+  } else {
+    // MIXED: the band list; the FP64 band pass (one-warp blocks, band_warps
+    // per SM); the FP32 coherent pass as its programmatic dependent, which
+    // runs beside it; then the long rays
     k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
-    auto k1 = k_coherent<float, MODE_MIXED, float>;
-    k1<<<grid_of(k1), block, 0, stream>>>(p);
-    rec(1);
-    auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
-    k2<<<grid_of(k2), block, 0, stream>>>(p);
-    rec(2);
-    // FP64 band rays are few: one warp per block and one block per SM
-    // sub-partition, so every warp gets an FP64 unit of its own
     auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
     k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
-    rec(3);
-  } else {
-    // band list, then the FP64 band pass on the high-priority side stream
-    // concurrently with the FP32 coherent and long-ray passes
-    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
-    cudaEventRecord(ls.fork, stream);
-    cudaStreamWaitEvent(ls.side, ls.fork, 0);
-    if (ls.band_ev && ls.band_ev[0]) record(ls.band_ev[0], ls.side);
-    auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
-    k3<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
-    if (ls.band_ev && ls.band_ev[1]) record(ls.band_ev[1], ls.side);
-    cudaEventRecord(ls.join, ls.side);
     auto k1 = k_coherent<float, MODE_MIXED, float>;
-    k1<<<grid_of(k1), block, 0, stream>>>(p);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid_of(k1));
+    lc.blockDim = dim3((unsigned)block);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    cudaLaunchKernelEx(&lc, k1, p);
     rec(1);
     auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
-    cudaStreamWaitEvent(stream, ls.join, 0);
     rec(3);
   }
   return cudaGetLastError();

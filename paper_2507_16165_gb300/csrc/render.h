@@ -11,17 +11,18 @@ struct LaunchShape {
   int num_sms;        // streaming multiprocessors of the device
   int block;          // threads per block
   int blocks_per_sm;  // 0: the occupancy limit of each kernel
-  // MIXED only: side stream (high priority) and fork / join events that run
-  // the FP64 band pass next to the FP32 passes; band_ev[0..1] time it.
+  // Surrogate only: side stream (high priority) and fork / join events that
+  // run the FP64 band pass next to the surrogate pass; band_ev[0..1] time it.
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t* band_ev = nullptr;
-  int band_warps = 4;  // band-pass warps per SM (one-warp blocks)
+  int band_warps = 4;  // FP64 band warps per SM
   int band_rows = 0;   // image rows over all cameras (band list threads)
 };
 
-// Launch the kernels of one render (coherent pass, long-ray pass and, in
-// MIXED mode, the FP64 band pass) on `stream`.  ev[0..3], when non-null,
+// Launch the kernels of one render (MIXED: band list and FP64 band pass,
+// with the coherent pass as its programmatic dependent running beside it;
+// coherent pass; long-ray pass) on `stream`.  ev[0..3], when non-null,
 // are recorded before the first kernel and after each pass.
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
                           cudaEvent_t* ev);

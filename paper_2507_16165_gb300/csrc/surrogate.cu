@@ -918,7 +918,6 @@ extern "C" int bh_surrogate_load(bh_scene* sc, const char* path) {
 int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                      void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
                      const RenderConfig& cfg) {
-  (void)cfg;
   if (!sc->surr || !sc->surr->d_frag)
     return bh_fail(BH_E_NO_SURROGATE, "surrogate mode: no trained weights on this scene");
   if (sc->sk.ic != BH_IC_STATIC && sc->sk.ic != BH_IC_EUCLIDEAN)
@@ -940,6 +939,12 @@ int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int*
     if (e != cudaSuccess) return bh_cuda_fail(e, "surrogate: fallback list");
     s->list_cap = need;
   }
+  // the FP64 band pass runs on the side stream beside the surrogate pass
+  pr.ls.side = sc->side;
+  pr.ls.fork = sc->fork;
+  pr.ls.join = sc->join;
+  pr.ls.band_ev = sc->band_ev;
+  pr.ls.band_warps = cfg.band_warps;
   pr.p.mlp_frag = s->d_frag;
   pr.p.mlp_bias = s->d_bias;
   pr.p.surr_table = s->d_table;

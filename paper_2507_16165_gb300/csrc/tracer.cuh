@@ -76,6 +76,18 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Programmatic dependent launch: a kernel lets the next kernel of its
+// stream (launched with programmatic stream serialization) start once all
+// of its blocks have called pdl_launch_dependents; the dependent's
+// pdl_wait_primary returns when the first kernel has completed and its
+// memory operations are visible.  Both are no-ops without such a launch.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_primary() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Quotient and reciprocal square root: the hardware approximations in FP32
 // (a few ulp, far inside the FP32 passes' error budget), correctly rounded
 // in FP64.
