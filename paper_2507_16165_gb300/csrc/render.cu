@@ -95,9 +95,11 @@ __device__ __forceinline__ bool slot_pixel(const Params& p, long long q, int* ca
 // intersection, otherwise capture (ingoing) or escape along d.  At most a
 // pixel or two per image: kept out of line so it does not crowd the hot
 // code of the persistent kernels (measured 3% faster FP32, 7% mixed).
+// Returns the ray's flags; the caller counts them (the statistics stay in
+// registers only while no out-of-line call takes their address).
 template <typename R, typename OutR, bool SPP = false>
-__device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d[3], R cos_a, int out,
-                           unsigned aux, LocalStats& st, SppAcc* acc = nullptr) {
+__device__ __noinline__ unsigned radial_ray(const Params& p, const R P[3], const R d[3], R cos_a,
+                                            int out, unsigned aux, SppAcc* acc = nullptr) {
   const SceneK& s = p.s;
   const SceneR<R>& S = SR<R>(s);
   R best = R(INFINITY);
@@ -145,7 +147,7 @@ __device__ __noinline__ void radial_ray(const Params& p, const R P[3], const R d
       sky_rgb<R>(s.seed, th, ph, c);
     emit_ray<OutR, SPP>(p, out, OutR(th), OutR(ph), flags, c, acc);
   }
-  st.count_flag(flags);
+  return flags;
 }
 
 // Periastron of the orbit through the FP32 initial state (u0, v0): the
@@ -224,7 +226,7 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
   if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, CR<R>(c).ir, r, &b, &cos_a)) {
-    radial_ray<R, OutR, SPP>(p, P, d, cos_a, out, r.aux, st, acc);
+    st.count_flag(radial_ray<R, OutR, SPP>(p, P, d, cos_a, out, r.aux, acc));
     return false;
   }
   *b_out = b;
@@ -302,25 +304,40 @@ __global__ void __launch_bounds__(256) k_band_list(const __grid_constant__ Param
   st.flush(p.ws);
 }
 
-// Turning point of the FP32 orbit: v changes sign inside [0, 1] of H.
-// Newton on v(t) with dv/dt = h^2 accel(u), from the linear guess.
+// Periastron reset of the MIXED mode.  An accepted FP32 step has just
+// passed the turning point (v went from > 0 to <= 0), so its end lies a
+// distance d past the periastron of the orbit through (u_p, 0), u_p from the
+// FP64 cubic.  The end state is put on that orbit, so no FP32 drift of the
+// incoming leg is carried into the outgoing one.  The orbit is even about
+// the turning point (its odd derivatives vanish there), so with
+// F(u) = 3Mu^2 - u and F' = 6Mu - 1 taken at u_p,
+//   u(d) = u_p + F d^2/2 + F' F d^4/24 + (18M F^2 + F'^2 F) d^6/720,
+// the d^8 term below 2e-8 u_p for d <= 0.4 rad, and v(d) = du/dd.  d is the
+// root of v(d) = v_end (two Newton steps from d = v_end / F); outside the
+// FP64 band |F| >= 0.02 / M, so d follows from the end velocity with the
+// velocity's own relative accuracy.  The end velocity is kept; u and the
+// FSAL derivative are replaced.  NaN u_p (no turning point): no change.
 template <typename R>
-__device__ __forceinline__ R turning_t(const Hermite<R>& H, R M3) {
-  const R va = H.d_start(), vb = H.d_end();  // h-scaled derivatives at the ends
-  R t = va / (va - vb);
-  t = m_min(R(1), m_max(R(0), t));
-  for (int it = 0; it < 4; ++it) {
-    const R g = H.dval_t(t);
-    const R dg = H.h * H.h * accel(M3, H.val_t(t));
-    if (dg == R(0)) break;
-    const R tn = m_min(R(1), m_max(R(0), t - m_div(g, dg)));
-    const bool done = m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7);
-    t = tn;
-    if (done) break;
+__device__ __forceinline__ void periastron_reset(R M3, R up, R h, R& un, R& vn, R& fn) {
+  if (!(up == up)) return;
+  const R F0 = accel(M3, up);
+  const R F1 = m_fma(R(2) * M3, up, R(-1));
+  const R c2 = R(0.5) * F0;
+  const R c4 = F1 * F0 * R(1.0 / 24.0);
+  const R c6 = m_fma(R(6) * M3 * F0, F0, F1 * F1 * F0) * R(1.0 / 720.0);
+  R d = vn * m_rcp(F0);
+  for (int it = 0; it < 2; ++it) {
+    const R d2 = d * d;
+    const R g = m_fma(d, m_fma(d2, m_fma(d2, R(6) * c6, R(4) * c4), R(2) * c2), -vn);
+    const R dg = m_fma(d2, m_fma(d2, R(30) * c6, R(12) * c4), R(2) * c2);
+    d -= g * m_rcp(dg);
   }
-  return t;
+  d = m_min(m_max(d, R(0)), h);
+  const R d2 = d * d;
+  un = m_fma(d2, m_fma(d2, m_fma(d2, c6, c4), c2), up);
+  vn = d * m_fma(d2, m_fma(d2, R(6) * c6, R(4) * c4), R(2) * c2);
+  fn = accel(M3, un);
 }
-
 
 template <typename R, typename E>
 __device__ __forceinline__ void consider(int type, R ph, unsigned id, int& bt, R& bp, unsigned& bid) {
@@ -351,7 +368,7 @@ template <> struct EventT<double, MODE_BAND64> { using type = float; };
 // shift = 2 pi floor(pa / 2 pi), so they stay small in FP32.
 template <typename R, int MODE>
 __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& pb, R h,
-                            bool peri, Hit<R>& hit, LocalStats& st) {
+                            Hit<R>& hit, LocalStats& st) {
   using E = typename EventT<R, MODE>::type;
   constexpr bool narrow = sizeof(E) < sizeof(R);
   const SceneK& s = p.s;
@@ -362,33 +379,7 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
   const E pa_e = E(pa - shift);
   Hermite<E> H;
   H.make(pa_e, E(h), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
-  if (MODE == MODE_MIXED && peri) {
-    // periastron reset: the step passed the turning point at pa + tp h;
-    // replace its end state by the point of the orbit through (u_p, 0) there
-    // (u_p from the FP64 cubic), so no FP32 drift of the incoming leg is
-    // carried into the outgoing one.  The orbit is even about the turning
-    // point (u' = u''' = u^(5) = 0 there), so with d = (1 - tp) h and
-    // F(u) = 3Mu^2 - u:  u = u_p + F d^2/2 + F' F d^4/24
-    // + (18M F^2 + F'^2 F) d^6/720, F and F' = 6Mu - 1 taken at u_p; the
-    // d^8 term is below 2e-8 u_p for d <= 0.4.  The step keeps its length.
-    const E tp = turning_t<E>(H, M3);
-    if (tp > E(0) && r.up == r.up) {
-      const R M3r = SR<R>(s).M3;
-      const R d = (R(1) - R(tp)) * h, d2 = d * d;
-      const R F0 = accel(M3r, r.up);
-      const R F1 = m_fma(R(2) * M3r, r.up, R(-1));
-      const R c2 = R(0.5) * F0;
-      const R c4 = F1 * F0 * R(1.0 / 24.0);
-      const R c6 = m_fma(R(6) * M3r * F0, F0, F1 * F1 * F0) * R(1.0 / 720.0);
-      un = m_fma(d2, m_fma(d2, m_fma(d2, c6, c4), c2), r.up);
-      vn = d * m_fma(d2, m_fma(d2, R(6) * c6, R(4) * c4), R(2) * c2);
-      fn = accel(M3r, un);
-      H.make(pa_e, E(h), E(r.u), E(r.v), E(r.f), E(un), E(vn), E(fn));
-    }
-    r.aux |= kAuxPeriDone;
-    st.c[ST_PERI]++;
-  }
-  const R hs = R(H.h);  // length of the (possibly truncated) step
+  const R hs = R(H.h);
   int bt = -1;
   R bp = R(0);
   unsigned bid = 0;
@@ -459,19 +450,20 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     }
     return false;
   }
+  if (MODE == MODE_MIXED && p.peri_reset && (r.v > R(0)) && (vn <= R(0)) &&
+      !(r.aux & kAuxPeriDone)) {
+    periastron_reset<R>(S.M3, r.up, h, un, vn, fn);
+    r.aux |= kAuxPeriDone;
+    st.c[ST_PERI]++;
+  }
   R pb = r.phi + h;
   // u <= 0 (escape) or u >= u_capt (capture) in one test: |u - c| >= c with
   // c = u_capt / 2; node, sphere window and the phi cap through phi_evt
   const R c = R(0.5) * S.u_capt;
-  bool slow = (m_abs(un - c) >= c) | (pb >= r.phi_evt);
-  bool peri = false;
-  if (MODE == MODE_MIXED) {
-    peri = p.peri_reset && (r.v > R(0)) && (vn <= R(0)) && !(r.aux & kAuxPeriDone);
-    slow |= peri;
-  }
+  const bool slow = (m_abs(un - c) >= c) | (pb >= r.phi_evt);
   if (__builtin_expect(slow, 0)) {
     st.c[ST_EVENTS]++;
-    if (step_events<R, MODE>(p, r, un, vn, fn, pb, h, peri, hit, st)) return true;
+    if (step_events<R, MODE>(p, r, un, vn, fn, pb, h, hit, st)) return true;
   }
   r.u = un;
   r.v = vn;
