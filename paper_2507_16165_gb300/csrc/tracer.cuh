@@ -368,6 +368,16 @@ __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
 // ---------------------------------------------------------------------------
 // Per-ray state.
 // ---------------------------------------------------------------------------
+// Angular windows of the spheres that a ray's plane cuts (centre and
+// half-width, rad, from the set-up).  They are indexed by sphere and so live
+// in local memory; they are kept apart from the Ray so that the Ray itself
+// stays in registers (an indexed array inside it kept the whole struct in
+// local memory, with its fields stored at every step).
+struct SphWin {
+  float c[kMaxSph];
+  float d[kMaxSph];
+};
+
 template <typename R>
 struct Ray {
   R u, v, f, phi, h;     // state, FSAL derivative, azimuth, next step
@@ -378,8 +388,7 @@ struct Ray {
                          // before it need no event search
   R up;                  // periastron u of the orbit (MIXED reset), NaN if none
   unsigned sph_mask;     // spheres whose in-plane circle is non-empty
-  float wc[kMaxSph];     // angular window of each such sphere: centre ...
-  float wd[kMaxSph];     // ... and half-width (rad), from the set-up
+  SphWin* win;           // angular window of each such sphere
   int steps;             // attempted steps
   int out;               // output pixel index
   unsigned aux;          // BAND / FP64 provenance bits, periastron-done bit
@@ -428,15 +437,15 @@ __device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, 
   const float rp2 = fmaxf(0.0f, s.f.rad[k] * s.f.rad[k] - (s.f.c2[k] - rho2));
   float pc = m_atan2(cy, cx);
   if (pc < 0.0f) pc += 6.28318530717958647692f;
-  r.wc[k] = pc;
-  r.wd[k] = m_asin(fminf(1.0f, sqrtf(rp2 * rcp_approx(rho2)))) + 1e-4f;
+  r.win->c[k] = pc;
+  r.win->d[k] = m_asin(fminf(1.0f, sqrtf(rp2 * rcp_approx(rho2)))) + 1e-4f;
 }
 
 // The first window of sphere k whose end lies at or after phi_from:
 // returns its start, *we its end.
 template <typename R>
 __device__ __forceinline__ float sphere_window(const Ray<R>& r, int k, float phi_from, float* we) {
-  const float pc = r.wc[k], dp = r.wd[k];
+  const float pc = r.win->c[k], dp = r.win->d[k];
   const float m = ceilf((phi_from - pc - dp) * 0.15915494309189535f);
   *we = pc + dp + 6.28318530717958647692f * m;
   return pc - dp + 6.28318530717958647692f * m;
