@@ -17,6 +17,15 @@ template <typename R>
 struct SceneR {
   R M, M3, u_capt, b_crit, r_in, r_out;
   R c[kMaxSph][3], c2[kMaxSph], rad[kMaxSph], K[kMaxSph];
+  // Rays with impact parameter b > cull_b[k] never meet sphere k: an
+  // unbound orbit (b > 3 sqrt(3) M) stays at r >= r_p, its periastron, and
+  // b = r_p sqrt(r_p / (r_p - 2M)) exceeds r_p by at most 3 sqrt(3) M - 3M
+  // = 2.196M (at r_p = 3M; the excess falls to M as r_p grows), so
+  // r_p >= b - 2.2M; the ball |x - c_k| <= R_k lies within r <= |c_k| + R_k.
+  // cull_b = (|c_k| + R_k)(1 + 1e-5) + 2.25M, the margins covering the
+  // rounding of b; +inf when that is not above 3 sqrt(3) M (a sphere
+  // reaching inside about 3M, which captured orbits may meet).
+  R cull_b[kMaxSph];
 };
 
 // Camera constants in the kernel's arithmetic type.
@@ -204,6 +213,8 @@ inline void fill_scene_r(const SceneK& s, SceneR<R>* o) {
     o->c2[k] = R(s.c2[k]);
     o->rad[k] = R(s.R[k]);
     o->K[k] = R(s.K[k]);
+    const double cb = (std::sqrt(s.c2[k]) + s.R[k]) * (1.0 + 1e-5) + 2.25 * s.M;
+    o->cull_b[k] = cb > 1.001 * s.b_crit ? R(cb) : R(INFINITY);
   }
 }
 template <typename R>

@@ -424,6 +424,12 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   Params& p = *out;
   memset(&p, 0, sizeof p);
   p.s = sc->sk;
+  if (cfg.mode == BH_MODE_PAPER_EPS || cfg.mode == BH_MODE_PAPER_EPS_FP32) {
+    // the polyline's straight segments cut inside the orbit's periastron:
+    // no sphere is culled by the impact parameter there
+    for (int k = 0; k < kMaxSph; ++k) p.s.f.cull_b[k] = INFINITY;
+    for (int k = 0; k < kMaxSph; ++k) p.s.d.cull_b[k] = INFINITY;
+  }
   p.cams = sc->d_cams;
   p.n_cams = n_cams;
   p.tile_w = cfg.tile_w;

@@ -517,13 +517,14 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
       r.phi_node = (p0 > R(0)) ? p0 : Num<R>::pi;
     }
   }
-  // spheres cut by the plane
+  // spheres cut by the plane and not wholly inside the orbit's periastron
+  // (SceneR::cull_b)
   unsigned mask = 0;
 #pragma unroll
   for (int k = 0; k < kMaxSph; ++k) {
     if (k < s.n_sph) {
       const R sd = nx * S.c[k][0] + ny * S.c[k][1] + nz * S.c[k][2];
-      if (m_abs(sd) < S.rad[k]) mask |= 1u << k;
+      if (m_abs(sd) < S.rad[k] && b <= S.cull_b[k]) mask |= 1u << k;
     }
   }
   r.sph_mask = mask;

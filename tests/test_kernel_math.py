@@ -44,3 +44,23 @@ def test_arccos_polynomial_within_published_bound():
     for k in coeffs[1:]:
         p = p * a + k
     assert np.max(np.abs(np.sqrt(1.0 - a) * p - np.arccos(a))) < 2.5e-8
+
+
+def test_periastron_bound_behind_the_sphere_cull():
+    """The kernels drop sphere k from a ray's mask when b exceeds
+    (|c_k| + R_k)(1 + 1e-5) + 2.25M, relying on r_p >= b - 2.2M for every
+    unbound orbit: with b = r_p sqrt(r_p / (r_p - 2M)) from the first
+    integral at the turning point, b - r_p is largest (3 sqrt(3) - 3 =
+    2.196) at the photon orbit r_p = 3M and falls toward M at large r_p.
+    Checked on a dense grid of r_p, and against the cubic's middle root for
+    sampled b (the periastron the oracle solves for)."""
+    rp = np.concatenate([np.linspace(3.0, 4.0, 200001), np.geomspace(4.0, 1e8, 200001)])
+    excess = rp * np.sqrt(rp / (rp - 2.0)) - rp
+    assert excess.max() <= 3.0 * np.sqrt(3.0) - 3.0 + 1e-12 < 2.2
+    assert excess.min() > 1.0 - 1e-6
+    for b in np.geomspace(3.0 * np.sqrt(3.0) * (1 + 1e-9), 1e5, 400):
+        roots = np.sort(np.roots([2.0, -1.0, 0.0, 1.0 / b**2]).real)
+        r_p = 1.0 / roots[1]
+        assert r_p >= b - 2.2
+    src = open(os.path.join(os.path.dirname(SRC), "bh_types.cuh")).read()
+    assert "* (1.0 + 1e-5) + 2.25 * s.M" in src
