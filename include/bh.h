@@ -130,7 +130,7 @@ typedef struct bh_render_opts {
   double rtol, atol;  /* Dormand-Prince tolerances (0: 1e-10 / 1e-10 in FP64,
                          1e-5 / 1e-7 in FP32 and MIXED)                     */
   double band;        /* FP64 / fallback band half-width in b (0: 0.05 M)    */
-  double band_rtol;   /* rtol = atol of the MIXED FP64 band pass (0: 1e-9)   */
+  double band_rtol;   /* rtol = atol of the MIXED FP64 band pass (0: 1e-8)   */
   double phi_max;     /* azimuth cap in rad (0: 64)                          */
   int max_steps;      /* attempted-step cap per ray (0: 100000)              */
   double h_max;       /* largest step in rad (0: none in FP64, 0.3 otherwise;
@@ -142,8 +142,10 @@ typedef struct bh_render_opts {
   int tile_w, tile_h; /* pixel tile that one warp takes (tile_w*tile_h = 32)*/
   int budget;         /* steps a ray may take in the coherent pass before it
                          moves to the long-ray queue                        */
-  int periastron_reset; /* MIXED: 1 = reset state at the turning point (default),
-                           -1 = off                                         */
+  int periastron_reset; /* MIXED: reset the state at the turning point from
+                           the FP64 periastron: 1 (or 0) = for rays with
+                           |b - 3 sqrt(3) M| < 2M (default), 2 = for every
+                           ray with a turning point, -1 = off               */
   uint32_t abort_after; /* fault injection: stop after this many work items
                            and report BH_E_DEVICE (0 = off)                 */
   double h_max_far;   /* largest step in rad for rays with |b - 3 sqrt(3) M|

@@ -322,7 +322,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.rtol = o->rtol > 0 ? o->rtol : (f64 ? 1e-10 : 1e-5);
   c.atol = o->atol > 0 ? o->atol : (f64 ? 1e-10 : 1e-7);
   c.band = o->band > 0 ? o->band : 0.05;
-  c.band_rtol = o->band_rtol > 0 ? o->band_rtol : 1e-9;
+  c.band_rtol = o->band_rtol > 0 ? o->band_rtol : 1e-8;
   c.phi_max = o->phi_max > 0 ? o->phi_max : 64.0;
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
   c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
@@ -340,7 +340,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   if (c.spp_n > 1) c.budget = c.max_steps;  // every sample finishes in the tile pass
   c.band_lanes = t.band_lanes;
   c.band_warps = t.band_warps;
-  c.peri_reset = o->periastron_reset >= 0 ? 1 : 0;
+  c.peri_reset = o->periastron_reset < 0 ? 0 : (o->periastron_reset == 2 ? 2 : 1);
   c.abort_after = o->abort_after;
   return c;
 }

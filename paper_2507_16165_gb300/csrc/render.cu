@@ -231,17 +231,27 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   }
   *b_out = b;
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
-  if (MODE == MODE_MIXED)
-    r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
+  const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
+  // rays at least kFarB from the critical impact parameter, whose exit
+  // directions amplify stepping errors far less
+  const bool far = !d64 && m_abs(b - SR<R>(p.s).b_crit) >= R(kFarB) * SR<R>(p.s).M;
+  if (MODE == MODE_MIXED) {
+    // the FP64 turning point of near-critical rays (all rays with
+    // peri_reset == 2); the others step through it in FP32
+    if (p.peri_reset == 2 || (p.peri_reset == 1 && !far)) {
+      r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
+    } else {
+      r.up = R(NAN);
+      r.aux |= kAuxPeriDone;
+    }
+  }
   r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), tol.phi_max);
   r.steps = 0;
-  const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
   // FP64 mirrors the oracle's starting step; FP32 starts at the step cap
   // (the controller shrinks it when the first attempt is rejected)
   r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01)) : tol.h_max;
-  // FP32 rays far from the photon sphere may take longer steps (their exit
-  // directions amplify stepping errors far less); they still start at h_max
-  if (!d64 && m_abs(b - SR<R>(p.s).b_crit) >= R(kFarB) * SR<R>(p.s).M) r.aux |= kAuxFar;
+  // far FP32 rays may take longer steps; they still start at h_max
+  if (far) r.aux |= kAuxFar;
   return true;
 }
 
@@ -450,8 +460,7 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     }
     return false;
   }
-  if (MODE == MODE_MIXED && p.peri_reset && (r.v > R(0)) && (vn <= R(0)) &&
-      !(r.aux & kAuxPeriDone)) {
+  if (MODE == MODE_MIXED && (r.v > R(0)) && (vn <= R(0)) && !(r.aux & kAuxPeriDone)) {
     periastron_reset<R>(S.M3, r.up, h, un, vn, fn);
     r.aux |= kAuxPeriDone;
     st.c[ST_PERI]++;
