@@ -150,7 +150,7 @@ typedef struct bh_render_opts {
                            and report BH_E_DEVICE (0 = off)                 */
   double h_max_far;   /* largest step in rad for rays with |b - 3 sqrt(3) M|
                          >= 2M in the FP32 passes, whose outputs are far less
-                         sensitive to stepping errors (0: 0.4; FP64: h_max) */
+                         sensitive to stepping errors (0: 0.5; FP64: h_max) */
   double paper_eps;   /* fixed step in rad of the BH_MODE_PAPER_EPS modes
                          (0: 0.01)                                          */
   int spp;            /* samples per pixel, a square n*n (0 or 1: one ray
@@ -168,6 +168,10 @@ typedef struct bh_render_opts {
                          angular momentum about z; the colour ramp is taken
                          at g t and scaled by g^3 (g = 0 inside 3M).  The
                          integrator modes only (else BH_E_UNSUPPORTED)      */
+  double rtol_far;    /* rtol of rays with |b - 3 sqrt(3) M| >= 2M in the FP32
+                         passes (their atol scales with it); their exit
+                         directions amplify local errors far less (0: 10 x
+                         rtol; FP64: rtol)                                  */
 } bh_render_opts;
 
 typedef struct bh_stats {

@@ -59,7 +59,8 @@ class bh_render_opts(ctypes.Structure):
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
                 ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double),
-                ("spp", ctypes.c_int), ("doppler", ctypes.c_int)]
+                ("spp", ctypes.c_int), ("doppler", ctypes.c_int),
+                ("rtol_far", ctypes.c_double)]
 
 
 class bh_stats(ctypes.Structure):

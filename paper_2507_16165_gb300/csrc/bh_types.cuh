@@ -44,10 +44,11 @@ template <typename R>
 struct TolR {
   R rtol, atol, phi_max, h_max, band;
   R h_far;  // step cap of rays with |b - b_c| >= kFarB (FP32 passes)
+  R far_e2; // (rtol / rtol_far)^2: their squared error norm is scaled by it
 };
 
 // Rays at least this far from the critical impact parameter (units of M)
-// take the relaxed step cap h_far in the FP32 passes.
+// take the relaxed step cap h_far and tolerance rtol_far in the FP32 passes.
 constexpr double kFarB = 2.0;
 
 // Scene constants, passed by value in every kernel's parameter block.
@@ -168,6 +169,7 @@ struct Params {
   double phi_max;
   double h_max;                 // step-size cap of the main pass (FP64 band: none)
   double h_max_far;             // FP32 step cap of rays with |b - b_c| >= kFarB
+  double rtol_far;              // FP32 rtol of those rays (atol scaled alike)
   double paper_eps;             // fixed step of the polyline modes
   int spp_n;                    // samples per pixel side (n x n), 1 = one centre ray
   int doppler;                  // Keplerian disk shading

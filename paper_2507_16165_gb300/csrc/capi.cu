@@ -263,7 +263,7 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
       opts->block_size != 256)
     return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
-      opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 ||
+      opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 || opts->rtol_far < 0 ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0 || opts->spp < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
   if (opts->spp > 1) {
@@ -325,7 +325,8 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.band_rtol = o->band_rtol > 0 ? o->band_rtol : 1e-8;
   c.phi_max = o->phi_max > 0 ? o->phi_max : 64.0;
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
-  c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.4);
+  c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.5);
+  c.rtol_far = o->rtol_far > 0 ? o->rtol_far : (f64 ? c.rtol : 10.0 * c.rtol);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
   c.paper_eps = o->paper_eps > 0 ? o->paper_eps : 0.01;
   c.doppler = o->doppler ? 1 : 0;
@@ -445,6 +446,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.phi_max = cfg.phi_max;
   p.h_max = cfg.h_max;
   p.h_max_far = cfg.h_max_far;
+  p.rtol_far = cfg.rtol_far;
   p.paper_eps = cfg.paper_eps;
   p.spp_n = cfg.spp_n;
   p.doppler = cfg.doppler;
@@ -462,10 +464,11 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
 }
 
 void fill_tolerances(Params& p) {
+  const double e = p.rtol_far > 0 ? p.rtol / p.rtol_far : 1.0;
   p.tf = TolR<float>{(float)p.rtol, (float)p.atol, (float)p.phi_max, (float)p.h_max, (float)p.band,
-                     (float)p.h_max_far};
-  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band, p.h_max_far};
-  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band, INFINITY};
+                     (float)p.h_max_far, (float)(e * e)};
+  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band, p.h_max_far, e * e};
+  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band, INFINITY, 1.0};
 }
 
 extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cams, const int* w,

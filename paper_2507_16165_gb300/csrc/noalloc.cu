@@ -124,7 +124,7 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   if (opts->block_size && opts->block_size != 64 && opts->block_size != 128 &&
       opts->block_size != 256)
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: block_size must be 64, 128 or 256");
-  if (opts->rtol < 0 || opts->atol < 0 || opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 ||
+  if (opts->rtol < 0 || opts->atol < 0 || opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->rtol_far < 0 ||
       opts->max_steps < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: negative option");
   SceneK sk;
@@ -199,7 +199,8 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   p.band = 0.0;
   p.phi_max = opts->phi_max > 0 ? opts->phi_max : 64.0;
   p.h_max = opts->h_max > 0 ? opts->h_max : (f64 ? INFINITY : 0.3);
-  p.h_max_far = opts->h_max_far > 0 ? opts->h_max_far : (f64 ? p.h_max : 0.4);
+  p.h_max_far = opts->h_max_far > 0 ? opts->h_max_far : (f64 ? p.h_max : 0.5);
+  p.rtol_far = opts->rtol_far > 0 ? opts->rtol_far : (f64 ? p.rtol : 10.0 * p.rtol);
   p.max_steps = opts->max_steps > 0 ? opts->max_steps : 100000;
   p.budget = p.max_steps;  // every ray finishes in the coherent pass
   p.peri_reset = 0;

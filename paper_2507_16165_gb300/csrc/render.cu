@@ -443,6 +443,9 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
   R un, vn, fn, err2;
   dp5_attempt<R>(S.M3, r.u, r.v, r.f, r.h, tol.rtol, tol.atol, un, vn, fn, err2);
+  // rays far from the critical impact parameter (FP32 passes only) are held
+  // to rtol_far, atol scaled alike: their error norm scales by rtol/rtol_far
+  if (r.aux & kAuxFar) err2 *= tol.far_e2;
   r.steps++;
   st.c[ST_STEPS]++;
   if (sizeof(R) == 8) st.c[ST_STEPS64]++;

@@ -47,7 +47,7 @@ struct bh_scene {
 // Resolved options of one render.
 struct RenderConfig {
   int mode;
-  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, paper_eps;
+  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, rtol_far, paper_eps;
   int spp_n;  // samples per pixel side
   int doppler;
   int max_steps;
