@@ -68,6 +68,7 @@ struct SceneK {
   unsigned long long seed;
   int ic;
   const uint32_t* sky_tex;  // equirectangular RGBA8 sky image, or null: checker
+  const float4* sky_lut;    // checker: the 512 cell colours (rgb), or null
   int sky_w, sky_h;
   SceneR<float> f;
   SceneR<double> d;

@@ -127,6 +127,10 @@ extern "C" int bh_scene_create(const bh_scene_desc* desc, bh_scene** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, sc->device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&sc->d_ws, sizeof(WorkK));
   if (e == cudaSuccess) e = cudaMemset(sc->d_ws, 0, sizeof(WorkK));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sc->d_sky_lut, 512 * sizeof(float4));
+  if (e == cudaSuccess) e = fill_sky_lut(k.seed, sc->d_sky_lut, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) k.sky_lut = sc->d_sky_lut;
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->ev[i]);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->band_ev[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->fork, cudaEventDisableTiming);
@@ -189,6 +193,7 @@ extern "C" void bh_scene_destroy(bh_scene* sc) {
     cudaFree(sc->d_stage_flags);
     cudaFree(sc->d_stage_rgba);
     cudaFree(sc->d_sky);
+    cudaFree(sc->d_sky_lut);
     for (int i = 0; i < 4; ++i)
       if (sc->ev[i]) cudaEventDestroy(sc->ev[i]);
     for (int i = 0; i < 2; ++i)

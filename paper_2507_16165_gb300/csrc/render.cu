@@ -144,7 +144,7 @@ __device__ __forceinline__ unsigned radial_ray(const Params& p, const R P[3], co
     if (s.sky_tex)
       sky_image_rgb<R>(s, th, ph, c);
     else
-      sky_rgb<R>(s.seed, th, ph, c);
+      sky_rgb<R>(s, th, ph, c);
     emit_ray<OutR, SPP>(p, out, OutR(th), OutR(ph), flags, c, acc);
   }
   return flags;
@@ -238,10 +238,12 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   if (MODE == MODE_MIXED) {
     // the FP64 turning point of near-critical rays (all rays with
     // peri_reset == 2); the others step through it in FP32
-    if (p.peri_reset == 2 || (p.peri_reset == 1 && !far)) {
+    if ((p.peri_reset == 2 || (p.peri_reset == 1 && !far)) && r.v > R(0)) {
       r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
+      r.tp = R(0);
     } else {
       r.up = R(NAN);
+      r.tp = R(-INFINITY);
       r.aux |= kAuxPeriDone;
     }
   }
@@ -463,19 +465,24 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
     }
     return false;
   }
-  if (MODE == MODE_MIXED && (r.v > R(0)) && (vn <= R(0)) && !(r.aux & kAuxPeriDone)) {
-    periastron_reset<R>(S.M3, r.up, h, un, vn, fn);
-    r.aux |= kAuxPeriDone;
-    st.c[ST_PERI]++;
-  }
   R pb = r.phi + h;
   // u <= 0 (escape) or u >= u_capt (capture) in one test: |u - c| >= c with
-  // c = u_capt / 2; node, sphere window and the phi cap through phi_evt
+  // c = u_capt / 2; node, sphere window and the phi cap through phi_evt;
+  // in MIXED the first step past the turning point (vn <= tp)
   const R c = R(0.5) * S.u_capt;
-  const bool slow = (m_abs(un - c) >= c) | (pb >= r.phi_evt);
+  bool slow = (m_abs(un - c) >= c) | (pb >= r.phi_evt);
+  if (MODE == MODE_MIXED) slow |= vn <= r.tp;
   if (__builtin_expect(slow, 0)) {
-    st.c[ST_EVENTS]++;
-    if (step_events<R, MODE>(p, r, un, vn, fn, pb, h, hit, st)) return true;
+    if (MODE == MODE_MIXED && vn <= r.tp) {
+      periastron_reset<R>(S.M3, r.up, h, un, vn, fn);
+      r.aux |= kAuxPeriDone;
+      r.tp = R(-INFINITY);
+      st.c[ST_PERI]++;
+    }
+    if ((m_abs(un - c) >= c) | (pb >= r.phi_evt)) {
+      st.c[ST_EVENTS]++;
+      if (step_events<R, MODE>(p, r, un, vn, fn, pb, h, hit, st)) return true;
+    }
   }
   r.u = un;
   r.v = vn;
@@ -544,6 +551,7 @@ __device__ bool restore_ray(const Params& p, long long q, const Spill<R>* sp, Ra
     r.phi = sp->phi;
     r.h = sp->h;
     r.f = accel(SR<R>(p.s).M3, r.u);
+    if (r.aux & kAuxPeriDone) r.tp = R(-INFINITY);
     for (int it = 0; it < 64 && r.phi_node <= r.phi; ++it) r.phi_node += Num<R>::pi;
     if (r.sph_mask) r.phi_sph = next_sphere_window<R>(r, r.phi);
     r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), TolPick<R, MODE>::get(p).phi_max);
@@ -994,9 +1002,22 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_paper(const __grid_const
   st.flush(p.ws);
 }
 
+__global__ void k_sky_lut(unsigned long long seed, float4* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= 512) return;
+  float rgb[3];
+  sky_cell_rgb(seed, c >> 5, c & 31, rgb);
+  out[c] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launch.
 // ---------------------------------------------------------------------------
+cudaError_t fill_sky_lut(unsigned long long seed, float4* out, cudaStream_t stream) {
+  k_sky_lut<<<4, 128, 0, stream>>>(seed, out);
+  return cudaGetLastError();
+}
+
 template <typename K>
 static int occupancy(K kernel, int block) {
   int n = 0;

@@ -34,6 +34,10 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
 cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_t stream,
                              cudaEvent_t* ev);
 
+// Fill the 512 checker-sky cell colours of a scene (16 x 32, row i = theta
+// cell, column j = phi cell) on `stream`.
+cudaError_t fill_sky_lut(unsigned long long seed, float4* out, cudaStream_t stream);
+
 // Launch only the coherent pass (mode MODE_FP32 or MODE_FP64).  With
 // p.budget >= p.max_steps no ray is moved to the long-ray list, so the pass
 // finishes every ray itself and needs no spill or band storage.

@@ -42,6 +42,7 @@ struct bh_scene {
   bool band_used = false;  // last render ran the side-stream band pass
   SurrogateState* surr = nullptr;
   uint32_t* d_sky = nullptr;  // sky image texels (bh_scene_sky_texture)
+  float4* d_sky_lut = nullptr;  // checker cell colours (SceneK::sky_lut)
 };
 
 // Resolved options of one render.

@@ -387,6 +387,7 @@ struct Ray {
   R phi_evt;             // min(phi_node, phi_sph, phi_max): steps ending
                          // before it need no event search
   R up;                  // periastron u of the orbit (MIXED reset), NaN if none
+  R tp;                  // MIXED: 0 while the turning-point reset is pending, else -inf
   unsigned sph_mask;     // spheres whose in-plane circle is non-empty
   SphWin* win;           // angular window of each such sphere
   int steps;             // attempted steps
@@ -693,12 +694,9 @@ __device__ __noinline__ void sky_image_rgb(const SceneK& s, R theta, R phi, floa
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void sky_rgb(unsigned long long seed, R theta, R phi, float rgb[3]) {
-  int i = (int)m_floor(theta * R(5.09295817894065074));   // 16 / pi
-  int j = (int)m_floor(phi * R(5.09295817894065074));     // 32 / (2 pi)
-  i = min(15, max(0, i));
-  j = min(31, max(0, j));
+// Colour of sky cell (i, j): parity picks the base colour, a splitmix64
+// hash of the seed and the cell tints each channel.
+__device__ __forceinline__ void sky_cell_rgb(unsigned long long seed, int i, int j, float rgb[3]) {
   const bool light = ((i + j) & 1) == 0;
   const unsigned long long hsh = splitmix64(seed * 2654435761ull + (unsigned long long)(32 * i + j));
   const float base[3] = {light ? 0.9f : 0.1f, light ? 0.9f : 0.1f, light ? 0.9f : 0.25f};
@@ -710,11 +708,23 @@ __device__ __forceinline__ void sky_rgb(unsigned long long seed, R theta, R phi,
   }
 }
 
+// Checkerboard sky: the 16 x 32 cells in (theta, phi); the cell colours come
+// from the scene's table of the 512 cell colours (made by sky_cell_rgb when
+// the scene is created), or are computed when the scene has none.
 template <typename R>
-__device__ __forceinline__ unsigned sky_rgba(unsigned long long seed, R theta, R phi) {
-  float rgb[3];
-  sky_rgb<R>(seed, theta, phi, rgb);
-  return pack_rgba(rgb[0], rgb[1], rgb[2]);
+__device__ __forceinline__ void sky_rgb(const SceneK& s, R theta, R phi, float rgb[3]) {
+  int i = (int)m_floor(theta * R(5.09295817894065074));   // 16 / pi
+  int j = (int)m_floor(phi * R(5.09295817894065074));     // 32 / (2 pi)
+  i = min(15, max(0, i));
+  j = min(31, max(0, j));
+  if (s.sky_lut) {
+    const float4 t = __ldg(&s.sky_lut[32 * i + j]);
+    rgb[0] = t.x;
+    rgb[1] = t.y;
+    rgb[2] = t.z;
+  } else {
+    sky_cell_rgb(s.seed, i, j, rgb);
+  }
 }
 
 // Colour accumulator of one pixel rendered with several samples: the
@@ -827,7 +837,7 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit,
     if (s.sky_tex)
       sky_image_rgb<T>(s, th, ph, c);
     else
-      sky_rgb<T>(s.seed, th, ph, c);
+      sky_rgb<T>(s, th, ph, c);
   } else if (fl == BH_FLAG_DISK) {
     const float rr = (float)(R(1) / hit.u);
     float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
