@@ -74,6 +74,7 @@ extern "C" {
                                segments between the points, objects found by
                                segment intersection; FP64 (the paper's
                                precision), directions stored as double     */
+#define BH_MAX_HOST_STRIPS 16
 #define BH_MODE_PAPER_EPS_FP32 5 /* the same in FP32, directions as float  */
 
 /* ---- initial-condition conventions (Sec. 2.2 reading) ---------------- */
@@ -172,6 +173,11 @@ typedef struct bh_render_opts {
                          passes (their atol scales with it); their exit
                          directions amplify local errors far less (0: 10 x
                          rtol; FP64: rtol)                                  */
+  int host_strips;    /* bh_render_host: the frame is rendered in this many
+                         strips of whole tile rows, each copied to the host
+                         while the next renders (0: about 2^21 rays a strip;
+                         at most BH_MAX_HOST_STRIPS; the surrogate renders
+                         whole)                                             */
 } bh_render_opts;
 
 typedef struct bh_stats {

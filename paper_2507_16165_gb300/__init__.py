@@ -19,7 +19,7 @@ from . import _capi
 from ._capi import (BH_FLAG_BAND, BH_FLAG_CAPT, BH_FLAG_DISK, BH_FLAG_ESC,  # noqa: F401
                     BH_FLAG_FP64, BH_FLAG_SPHERE, BH_FLAG_STEP_LIMIT, BH_FLAG_SURR,
                     BH_MODE_FP32, BH_MODE_FP64, BH_MODE_MIXED, BH_MODE_PAPER_EPS,
-                    BH_MODE_PAPER_EPS_FP32, BH_MODE_SURROGATE, MODES,
+                    BH_MAX_HOST_STRIPS, BH_MODE_PAPER_EPS_FP32, BH_MODE_SURROGATE, MODES,
                     BHError, check)
 
 __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",

@@ -14,6 +14,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libbh.so")
 
 BH_MAX_SPHERES = 8
+BH_MAX_HOST_STRIPS = 16
 BH_OK = 0
 BH_E_INVALID, BH_E_NOMEM, BH_E_CUDA, BH_E_DEVICE = -1, -2, -3, -4
 BH_E_NO_SURROGATE, BH_E_IO, BH_E_UNSUPPORTED = -5, -6, -7
@@ -60,7 +61,7 @@ class bh_render_opts(ctypes.Structure):
                 ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
                 ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double),
                 ("spp", ctypes.c_int), ("doppler", ctypes.c_int),
-                ("rtol_far", ctypes.c_double)]
+                ("rtol_far", ctypes.c_double), ("host_strips", ctypes.c_int)]
 
 
 class bh_stats(ctypes.Structure):

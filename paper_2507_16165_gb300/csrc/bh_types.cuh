@@ -162,7 +162,8 @@ struct Params {
   int n_cams;
   int tile_w, tile_h;
   int budget;
-  long long n_queue;  // queue slots
+  long long n_queue;  // queue slots: the pass takes slots [q_begin, n_queue)
+  long long q_begin;  // first slot (0; a later window when a render is split into strips)
   long long n_rays;   // output rays
   double rtol, atol;            // integrator tolerances of the main pass
   double rtol64, atol64;        // FP64 band tolerances (MIXED)

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -135,6 +136,9 @@ extern "C" int bh_scene_create(const bh_scene_desc* desc, bh_scene** out) {
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&sc->band_ev[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->join, cudaEventDisableTiming);
+  for (int i = 0; i < BH_MAX_HOST_STRIPS && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&sc->strip_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sc->copy, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
@@ -201,6 +205,9 @@ extern "C" void bh_scene_destroy(bh_scene* sc) {
     if (sc->fork) cudaEventDestroy(sc->fork);
     if (sc->join) cudaEventDestroy(sc->join);
     if (sc->side) cudaStreamDestroy(sc->side);
+    for (int i = 0; i < BH_MAX_HOST_STRIPS; ++i)
+      if (sc->strip_ev[i]) cudaEventDestroy(sc->strip_ev[i]);
+    if (sc->copy) cudaStreamDestroy(sc->copy);
     surrogate_release(sc);
   }
   delete sc;
@@ -269,6 +276,7 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
     return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
       opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 || opts->rtol_far < 0 ||
+      opts->host_strips < 0 || opts->host_strips > BH_MAX_HOST_STRIPS ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0 || opts->spp < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
   if (opts->spp > 1) {
@@ -486,6 +494,55 @@ extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cam
   return render_device(sc, cams, n_cams, w, h, out_dirs, out_flags, out_rgba8, opts);
 }
 
+// One strip of a host render: queue slots [q_lo, q_hi) (whole tile rows),
+// image rows [row_lo, row_hi) numbered over all cameras, outputs [o_lo, o_hi).
+struct HostStrip {
+  long long q_lo, q_hi, o_lo, o_hi;
+  int row_lo, row_hi;
+};
+
+// Cut the prepared cameras' tile rows into at most `want` strips of about
+// equal slot counts (want = 0: about 2^21 rays a strip).
+static int cut_strips(const bh_scene* sc, int n_cams, int tile_h, long long n_queue, int want,
+                      HostStrip* out) {
+  if (want <= 0) want = (int)std::min<long long>(BH_MAX_HOST_STRIPS, std::max(1LL, n_queue >> 21));
+  const long long target = (n_queue + want - 1) / want;
+  int n = 0;
+  HostStrip cur{0, 0, 0, 0, 0, 0};
+  for (int ci = 0; ci < n_cams; ++ci) {
+    const CamK& c = sc->h_cams[ci];
+    for (int ty = 0; ty < c.tiles_y; ++ty) {
+      const int y1 = std::min(c.h, (ty + 1) * tile_h);
+      cur.q_hi = c.q_off + (long long)(ty + 1) * c.tiles_x * 32;
+      cur.o_hi = c.out_off + (long long)y1 * c.w;
+      cur.row_hi = c.row_off + y1;
+      const bool last = ci == n_cams - 1 && ty == c.tiles_y - 1;
+      if (last || (cur.q_hi - cur.q_lo >= target && n < want - 1)) {
+        out[n++] = cur;
+        cur = HostStrip{cur.q_hi, cur.q_hi, cur.o_hi, cur.o_hi, cur.row_hi, cur.row_hi};
+      }
+    }
+  }
+  return n;
+}
+
+// Whether image rows [row_lo, row_hi) of a strip may hold MIXED band pixels:
+// a row meets the band annulus rho^2 in (band_rho2_lo, band_rho2_hi) only if
+// the squared image-plane height of its pixel centres is below band_rho2_hi
+// (the test k_band_list makes, here with a margin).
+static bool strip_has_band(const bh_scene* sc, int n_cams, const HostStrip& t) {
+  for (int ci = 0; ci < n_cams; ++ci) {
+    const CamK& c = sc->h_cams[ci];
+    if (!(c.band_rho2_hi > c.band_rho2_lo)) continue;
+    const int y0 = std::max(0, t.row_lo - c.row_off), y1 = std::min(c.h, t.row_hi - c.row_off);
+    for (int y = y0; y < y1; ++y) {
+      const double sy = c.sy - (y + 0.5) * 2.0 * c.sy / c.h;
+      if (sy * sy < 1.001 * c.band_rho2_hi + 1e-12) return true;
+    }
+  }
+  return false;
+}
+
 extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int n_cams,
                               const int* w, const int* h, void* host_dirs, uint16_t* host_flags,
                               uint32_t* host_rgba8, const bh_render_opts* opts) {
@@ -501,17 +558,99 @@ extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int 
   if (e == cudaSuccess) e = grow(&sc->d_stage_flags, &sc->stage_flags_cap, (size_t)n);
   if (e == cudaSuccess) e = grow(&sc->d_stage_rgba, &sc->stage_rgba_cap, (size_t)n);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_host: staging allocation");
-  rc = render_device(sc, cams, n_cams, w, h, host_dirs ? sc->d_stage_dirs : nullptr,
-                     host_flags ? sc->d_stage_flags : nullptr, host_rgba8 ? sc->d_stage_rgba : nullptr,
-                     opts);
-  if (rc) return rc;
+  void* sd = host_dirs ? sc->d_stage_dirs : nullptr;
+  uint16_t* sf = host_flags ? sc->d_stage_flags : nullptr;
+  uint32_t* sr = host_rgba8 ? sc->d_stage_rgba : nullptr;
   cudaStream_t stream = (cudaStream_t)opts->stream;
-  if (host_dirs)
-    e = cudaMemcpyAsync(host_dirs, sc->d_stage_dirs, (size_t)(2 * n) * dsz, cudaMemcpyDeviceToHost, stream);
-  if (e == cudaSuccess && host_flags)
-    e = cudaMemcpyAsync(host_flags, sc->d_stage_flags, (size_t)n * 2, cudaMemcpyDeviceToHost, stream);
-  if (e == cudaSuccess && host_rgba8)
-    e = cudaMemcpyAsync(host_rgba8, sc->d_stage_rgba, (size_t)n * 4, cudaMemcpyDeviceToHost, stream);
+  // copies of output range [lo, hi) on stream s
+  auto copy_range = [&](long long lo, long long hi, cudaStream_t s) {
+    cudaError_t r = cudaSuccess;
+    const long long m = hi - lo;
+    if (m <= 0) return r;
+    if (host_dirs) {
+      char* hd = (char*)host_dirs;
+      const char* dd = (const char*)sc->d_stage_dirs;
+      r = cudaMemcpyAsync(hd + lo * dsz, dd + lo * dsz, m * dsz, cudaMemcpyDeviceToHost, s);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(hd + (n + lo) * dsz, dd + (n + lo) * dsz, m * dsz, cudaMemcpyDeviceToHost, s);
+    }
+    if (r == cudaSuccess && host_flags)
+      r = cudaMemcpyAsync(host_flags + lo, sc->d_stage_flags + lo, m * 2, cudaMemcpyDeviceToHost, s);
+    if (r == cudaSuccess && host_rgba8)
+      r = cudaMemcpyAsync(host_rgba8 + lo, sc->d_stage_rgba + lo, m * 4, cudaMemcpyDeviceToHost, s);
+    return r;
+  };
+  if (opts->mode == BH_MODE_SURROGATE) {
+    // the surrogate pass renders whole, then copies
+    rc = render_device(sc, cams, n_cams, w, h, sd, sf, sr, opts);
+    if (rc) return rc;
+    e = copy_range(0, n, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_host: copy back");
+    return BH_OK;
+  }
+  // Strips of whole tile rows: strip k renders (its own slot window, band
+  // rows and long rays) on `stream` while strip k - 1's outputs are copied
+  // on the scene's copy stream, so the copy, which takes longer than the
+  // render at 14 B per ray, starts after the first strip instead of the
+  // frame.  Each ray is computed as in one whole render.
+  PreparedRender pr;
+  rc = prepare_render(sc, cams, n_cams, w, h, sd, sf, sr, opts, stream, nullptr, &pr);
+  if (rc) return rc;
+  HostStrip strips[BH_MAX_HOST_STRIPS];
+  const int ns = cut_strips(sc, n_cams, pr.p.tile_h, pr.p.n_queue, opts->host_strips, strips);
+  const bool mixed = pr.kmode == MODE_MIXED;
+  int regs_per_sm = 65536;
+  cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, sc->device);
+  e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
+  if (mixed && e == cudaSuccess) {
+    // MIXED: one band list and FP64 band pass over the whole frame on the
+    // side stream, beside the strips' FP32 passes (a band pass per strip
+    // would put the slowest band ray's latency into every strip); the copy
+    // of a strip that holds band pixels also waits for it
+    e = cudaEventRecord(sc->fork, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc->side, sc->fork, 0);
+    LaunchShape lb = pr.ls;
+    lb.mixed_part = 1;
+    if (e == cudaSuccess) e = launch_render(pr.p, pr.kmode, lb, sc->side, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(sc->join, sc->side);
+  }
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    const HostStrip& t = strips[k];
+    Params ps = pr.p;
+    ps.q_begin = t.q_lo;
+    ps.n_queue = t.q_hi;
+    LaunchShape ls = pr.ls;
+    ls.band_row0 = t.row_lo;
+    ls.band_rows = t.row_hi - t.row_lo;
+    if (mixed) {
+      ls.mixed_part = 2;
+      // leave the band warps their registers (both kernels hold 64 a
+      // thread): a strip launched without that room fills every SM and the
+      // band pass waits for it to retire
+      const int room = (regs_per_sm - ls.band_warps * 32 * 64) / (64 * ls.block);
+      ls.blocks_per_sm = std::max(1, ls.blocks_per_sm > 0 ? std::min(ls.blocks_per_sm, room) : room);
+    }
+    // the strip's queue counters (the band pass's run on beside it);
+    // statistics and status over the frame
+    if (k > 0) e = cudaMemsetAsync(sc->d_ws, 0, offsetof(WorkK, band_count), stream);
+    if (e == cudaSuccess) e = launch_render(ps, pr.kmode, ls, stream, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(sc->strip_ev[k], stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc->copy, sc->strip_ev[k], 0);
+    if (e == cudaSuccess && mixed && strip_has_band(sc, n_cams, t))
+      e = cudaStreamWaitEvent(sc->copy, sc->join, 0);
+    if (e == cudaSuccess) e = copy_range(t.o_lo, t.o_hi, sc->copy);
+  }
+  if (mixed && e == cudaSuccess) e = cudaStreamWaitEvent(stream, sc->join, 0);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(sc->copy);
+    cudaStreamSynchronize(sc->side);
+    return bh_cuda_fail(e, "bh_render_host: strips");
+  }
+  sc->last_stream = stream;
+  sc->timed = false;
+  sc->band_used = false;
+  e = cudaStreamSynchronize(sc->copy);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_host: copy back");
   return BH_OK;

@@ -262,12 +262,14 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
 // rho^2), its lanes test band_pixel on them and two pixels beyond each end,
 // and the warp appends the band rays' queue slots to the FP64 list with one
 // atomic per 32 columns.
-__global__ void __launch_bounds__(256) k_band_list(const __grid_constant__ Params p, int n_rows) {
+__global__ void __launch_bounds__(256) k_band_list(const __grid_constant__ Params p, int row0,
+                                                   int n_rows) {
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
   LocalStats st;
   st.zero();
-  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n_rows; row += warps) {
+  for (int row = row0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < row0 + n_rows;
+       row += warps) {
     int lo = 0, hi = p.n_cams - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
   st.zero();
   for (;;) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.ws->q_next, 32ull);
+    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
     base = __shfl_sync(kFull, base, 0);
     if (base >= (unsigned long long)p.n_queue) break;
     if (p.abort_after && base >= p.abort_after) {
@@ -723,7 +725,7 @@ __global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Pa
   st.zero();
   for (;;) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.ws->q_next, 32ull);
+    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
     base = __shfl_sync(kFull, base, 0);
     if (base >= (unsigned long long)p.n_queue) break;
     if (p.abort_after && base >= p.abort_after) {
@@ -973,7 +975,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_paper(const __grid_const
   st.zero();
   for (;;) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.ws->q_next, 32ull);
+    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
     base = __shfl_sync(kFull, base, 0);
     if (base >= (unsigned long long)p.n_queue) break;
     if (p.abort_after && base >= p.abort_after) {
@@ -1088,11 +1090,29 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     k2<<<grid_of(k2), block, 0, stream>>>(p);
     rec(2);
     rec(3);
+  } else if (ls.mixed_part == 1) {
+    // MIXED band only: the band list and the FP64 band pass
+    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_row0, ls.band_rows);
+    auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
+    k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
+    rec(1);
+    rec(2);
+    rec(3);
+  } else if (ls.mixed_part == 2) {
+    // MIXED without the band: the FP32 coherent pass (band pixels skipped)
+    // and the long rays
+    auto k1 = k_coherent<float, MODE_MIXED, float>;
+    k1<<<grid_of(k1), block, 0, stream>>>(p);
+    rec(1);
+    auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
+    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    rec(2);
+    rec(3);
   } else {
     // MIXED: the band list; the FP64 band pass (one-warp blocks, band_warps
     // per SM); the FP32 coherent pass as its programmatic dependent, which
     // runs beside it; then the long rays
-    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
+    k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_row0, ls.band_rows);
     auto k3 = k_longrays<double, MODE_BAND64, float, SRC_BAND>;
     k3<<<ls.band_warps * ls.num_sms, 32, 0, stream>>>(p);
     auto k1 = k_coherent<float, MODE_MIXED, float>;
@@ -1130,7 +1150,7 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
       cudaEventRecord(e, s);
   };
   if (ev) record(ev[0], stream);
-  k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_rows);
+  k_band_list<<<(ls.band_rows + 7) / 8, 256, 0, stream>>>(p, ls.band_row0, ls.band_rows);
   cudaEventRecord(ls.fork, stream);
   cudaStreamWaitEvent(ls.side, ls.fork, 0);
   if (ls.band_ev) record(ls.band_ev[0], ls.side);

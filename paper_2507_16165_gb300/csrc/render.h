@@ -17,7 +17,10 @@ struct LaunchShape {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t* band_ev = nullptr;
   int band_warps = 4;  // FP64 band warps per SM
-  int band_rows = 0;   // image rows over all cameras (band list threads)
+  int band_rows = 0;   // image rows the band list covers (band list threads) ...
+  int band_row0 = 0;   // ... starting at this row (rows numbered over all cameras)
+  int mixed_part = 0;  // MIXED: 0 = the whole render, 1 = band list and FP64 band
+                       // pass only, 2 = coherent and long-ray passes only
 };
 
 // Launch the kernels of one render (MIXED: band list and FP64 band pass,

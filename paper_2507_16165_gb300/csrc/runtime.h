@@ -43,6 +43,8 @@ struct bh_scene {
   SurrogateState* surr = nullptr;
   uint32_t* d_sky = nullptr;  // sky image texels (bh_scene_sky_texture)
   float4* d_sky_lut = nullptr;  // checker cell colours (SceneK::sky_lut)
+  cudaStream_t copy = nullptr;  // bh_render_host: copies of finished strips
+  cudaEvent_t strip_ev[BH_MAX_HOST_STRIPS] = {};
 };
 
 // Resolved options of one render.
