@@ -66,7 +66,9 @@ extern "C" {
 #define BH_MODE_FP64 0      /* FP64 everywhere                              */
 #define BH_MODE_FP32 1      /* FP32 everywhere                              */
 #define BH_MODE_MIXED 2     /* FP32 stepping; FP64 for the periastron reset
-                               and for rays with |b - 3 sqrt(3) M| < band   */
+                               of rays with |b - 3 sqrt(3) M| < 2M and the
+                               integration of rays with |b - 3 sqrt(3) M| <
+                               band                                         */
 #define BH_MODE_SURROGATE 3 /* MLP surrogate with integrator fallback       */
 #define BH_MODE_PAPER_EPS 4 /* the paper's own stepping (Sec. 2.1-2.2): fixed
                                steps paper_eps in phi with the classical
@@ -74,8 +76,10 @@ extern "C" {
                                segments between the points, objects found by
                                segment intersection; FP64 (the paper's
                                precision), directions stored as double     */
-#define BH_MAX_HOST_STRIPS 16
 #define BH_MODE_PAPER_EPS_FP32 5 /* the same in FP32, directions as float  */
+
+/* most strips a bh_render_host frame is cut into (bh_render_opts)          */
+#define BH_MAX_HOST_STRIPS 16
 
 /* ---- initial-condition conventions (Sec. 2.2 reading) ---------------- */
 #define BH_IC_STATIC 0    /* camera is a static observer (default)        */
@@ -251,9 +255,17 @@ int bh_render(const bh_scene *scene, const bh_camera *cams, int n_cams, const in
               const int *h, void *out_dirs, uint16_t *out_flags, uint32_t *out_rgba8,
               const bh_render_opts *opts);
 
-/* Same render into HOST buffers (pageable or pinned): renders into scene-
- * owned device staging, copies back and synchronises the stream before
- * returning.  Layouts as for bh_render. */
+/* Same render into HOST buffers (pageable or pinned; pinned copies are
+ * faster): renders into scene-owned device staging and copies back, then
+ * synchronises before returning.  Layouts as for bh_render, results
+ * identical to it.  The integrator modes render the frame in strips of
+ * whole tile rows (opts->host_strips) on opts->stream, each strip's outputs
+ * copied on a scene-owned copy stream while the next strip renders; the
+ * MIXED FP64 band pass runs once for the frame on the scene's side stream.
+ * The surrogate mode renders whole, then copies.  Kernel times are not
+ * recorded for bh_render_stats (its counts cover the whole frame).
+ * Errors: as bh_render; BH_E_INVALID for host_strips outside
+ * [0, BH_MAX_HOST_STRIPS]. */
 int bh_render_host(const bh_scene *scene, const bh_camera *cams, int n_cams, const int *w,
                    const int *h, void *host_dirs, uint16_t *host_flags,
                    uint32_t *host_rgba8, const bh_render_opts *opts);
