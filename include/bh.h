@@ -179,10 +179,9 @@ typedef struct bh_render_opts {
                          rtol; FP64: rtol)                                  */
   int host_strips;    /* bh_render_host: the frame is rendered in this many
                          strips of whole tile rows, each copied to the host
-                         while the next renders (0: about 2^21 rays a strip,
-                         the first three shorter -- a quarter, 0.4, 0.64 --
-                         so the copies start sooner; at most
-                         BH_MAX_HOST_STRIPS; the surrogate renders whole)   */
+                         while the next renders (0: about 2^21 rays a strip;
+                         at most BH_MAX_HOST_STRIPS; the surrogate renders
+                         whole)                                             */
 } bh_render_opts;
 
 typedef struct bh_stats {

@@ -501,21 +501,12 @@ struct HostStrip {
   int row_lo, row_hi;
 };
 
-// Cut the prepared cameras' tile rows into strips.  want > 0: at most want
-// strips of about equal slot counts.  want = 0: strips of about 2^21 rays,
-// the first ones smaller -- a quarter, then growing by 1.6 a strip -- since
-// the host render takes the first strip's render time plus the copy of the
-// whole frame; each strip still renders faster than its predecessor copies
-// (rendering produces 14 B per ray faster than the host link takes them,
-// about 1.7 times, so a strip at most 1.6 times its predecessor never
-// leaves the copy stream idle).
+// Cut the prepared cameras' tile rows into at most `want` strips of about
+// equal slot counts (want = 0: about 2^21 rays a strip).
 static int cut_strips(const bh_scene* sc, int n_cams, int tile_h, long long n_queue, int want,
                       HostStrip* out) {
-  const bool ramp = want <= 0;
-  // (the ramp's three short strips hold about 1.3 full ones: room is left for them)
-  if (ramp) want = (int)std::min<long long>(BH_MAX_HOST_STRIPS - 3, std::max(1LL, n_queue >> 21));
-  const long long full = (n_queue + want - 1) / want;
-  double grow = ramp && want > 1 ? 0.25 : 1.0;
+  if (want <= 0) want = (int)std::min<long long>(BH_MAX_HOST_STRIPS, std::max(1LL, n_queue >> 21));
+  const long long target = (n_queue + want - 1) / want;
   int n = 0;
   HostStrip cur{0, 0, 0, 0, 0, 0};
   for (int ci = 0; ci < n_cams; ++ci) {
@@ -526,12 +517,9 @@ static int cut_strips(const bh_scene* sc, int n_cams, int tile_h, long long n_qu
       cur.o_hi = c.out_off + (long long)y1 * c.w;
       cur.row_hi = c.row_off + y1;
       const bool last = ci == n_cams - 1 && ty == c.tiles_y - 1;
-      const long long target = (long long)(full * grow);
-      if (last || (cur.q_hi - cur.q_lo >= target && n < BH_MAX_HOST_STRIPS - 1 &&
-                   n_queue - cur.q_hi > 0 && (ramp || n < want - 1))) {
+      if (last || (cur.q_hi - cur.q_lo >= target && n < want - 1)) {
         out[n++] = cur;
         cur = HostStrip{cur.q_hi, cur.q_hi, cur.o_hi, cur.o_hi, cur.row_hi, cur.row_hi};
-        grow = std::min(1.0, grow * 1.6);
       }
     }
   }
