@@ -371,7 +371,11 @@ def run_ours(args) -> None:
         "peak": peak_tflops,
         "unit": "TFLOP/s",
         "frac": (achieved / peak_tflops) if achieved is not None else None,
-        "traffic": profile_traffic(args.form),
+        # DRAM bytes per launch from the ncu capture of this exact workload
+        # (the 4096^2 config-3 frame, default shading, one sample per pixel)
+        "traffic": profile_traffic(args.form) if (args.workload == "c3" and args.size == 4096
+                                                  and args.spp <= 1 and not args.sky_image
+                                                  and not args.doppler) else None,
         "kernel": ("k_paper" if paper else "k_coherent + k_longrays") + f" ({prec} {method} steps)",
         "peak_source": f"derived: {SM_COUNT} SMs x {lanes} {prec} FMA lanes x 2 FLOP x "
                        f"{sm_max:.0f} MHz (max SM clock)",
