@@ -53,9 +53,10 @@ FP64_LANES_PER_SM = 2
 FLOP_PER_RK4_STEP = 4 * 3 + 6 * 2 + 2 * 6 + 1
 STATED_ERROR = {"mixed": 1e-4, "fp32": 1e-4, "fp64": 1e-9, "surrogate": 1e-3,
                 "paper": 1e-4, "paper_fp32": 1e-4}
-# kernels one render launches: coherent + long-ray passes, and in MIXED the
-# band pre-pass and the FP64 band pass
-KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2, "surrogate": 4, "paper": 1,
+# kernels one render launches: tile + long-ray passes, and in MIXED the band
+# pre-pass and the FP64 band pass; the surrogate: band pre-pass, FP64 band
+# pass, surrogate pass, lock-step pass over its fallback list, long-ray pass
+KERNELS_PER_RENDER = {"mixed": 4, "fp32": 2, "fp64": 2, "surrogate": 5, "paper": 1,
                       "paper_fp32": 1}
 
 
@@ -258,6 +259,172 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# Forms of the metric measured beside the headline, each on its own workload
+# and options: (bh mode, workload, extra bh_render_opts, test asserting its
+# stated error).  c5 is the 64-camera orbit sequence in one graph replay with
+# the autotuned launch shape.
+FORMS = {
+    "fp64": ("fp64", "c3", {}, "tests/test_gpu_fullsize.py::c3_fp64_4096"),
+    "fp32": ("fp32", "c3", {}, "tests/test_gpu_fullsize.py::c3_fp32_4096"),
+    "mixed": ("mixed", "c3", {}, "tests/test_gpu_fullsize.py::c3_mixed_4096"),
+    "mixed_literal": ("mixed", "c3", {"periastron_reset": 2},
+                      "tests/test_gpu_fullsize.py::c3_mixed_literal_4096"),
+    "surrogate": ("surrogate", "c3", {}, "tests/test_gpu_fullsize.py::c4_surrogate_4096"),
+    "c5_fp32": ("fp32", "c5", {}, "tests/test_gpu_batch.py::test_batch64_full_size_sampled_parity[fp32]"),
+    "c5_surrogate": ("surrogate", "c5", {},
+                     "tests/test_gpu_batch.py::test_batch64_full_size_sampled_parity[surrogate]"),
+}
+# MLP work per evaluated ray (mlp.cuh): 304 mma.sync m16n8k16 per warp of 32
+# rays (BF16 high and low halves of every activation, 4 layers) x 4096 FLOP,
+# and one tanh.approx (one MUFU operation) per hidden activation, 3 x 64.
+MLP_FLOP_PER_RAY = 304 * 4096 // 32
+MLP_MUFU_PER_RAY = 3 * 64
+# special-function (MUFU) operations per SM and cycle on Blackwell: 4 per
+# SM sub-partition
+MUFU_PER_SM = 16
+
+
+class FormRun:
+    """One form of the renderer set up on its workload: scene, device
+    buffers, options and, for the 64-camera workload, the autotuned shape
+    captured in a CUDA graph."""
+
+    def __init__(self, bh, torch, form, wname, size, extra, stream, args):
+        self.bh, self.torch = bh, torch
+        self.form = form
+        self.w = workload(form, size, wname)
+        if args.sky_image:
+            from dataclasses import replace
+            self.w = replace(self.w, scene=replace(self.w.scene, sky_texture=W.sky_texture(0, 2048, 1024)))
+        w = self.w
+        self.n = w.n_rays
+        self.sc = bh.Scene(w.scene)
+        self.cams = self.sc.cameras(w.cameras)
+        self.wv = [c.w for c in w.cameras]
+        self.hv = [c.h for c in w.cameras]
+        self.stream = stream
+        self.f64 = form in ("fp64", "paper")
+        self.paper = form in ("paper", "paper_fp32")
+        n = self.n
+        self.dirs = torch.empty(2 * n, dtype=torch.float64 if self.f64 else torch.float32, device="cuda")
+        self.flags = torch.empty(n, dtype=torch.int16, device="cuda")
+        self.rgba = torch.empty(n, dtype=torch.int32, device="cuda")
+        self.extra = dict(extra)
+        self.opts = bh.render_opts(form, stream, rtol=w.rtol, atol=w.atol, band=w.band,
+                                   paper_eps=args.paper_eps, spp=args.spp,
+                                   doppler=int(args.doppler), **self.extra)
+        self.rays_per_pixel = args.spp + 1 if args.spp > 1 else 1
+        self.surrogate = None
+        if form == "surrogate":
+            # trained weights of the project (train_surrogate.py); training
+            # is reported separately and is not part of the timed region
+            path = os.path.join(ROOT, "paper_2507_16165_gb300", "data", "surrogate_m1.bin")
+            bh.bh_surrogate_load(self.sc.handle, path)
+            try:
+                with open(os.path.splitext(path)[0] + ".json") as f:
+                    self.surrogate = json.load(f)
+            except OSError:
+                self.surrogate = {"weights": path}
+        self.graph = None
+        self.tuned = None
+        if wname == "c5":
+            # autotune the launch shape on this workload, then capture the
+            # whole multi-camera render once and replay it
+            self.tuned = bh.bh_autotune(self.sc.handle, self.cams, self.wv, self.hv, self.dirs,
+                                        self.flags, self.rgba, self.opts)
+            self.graph = bh.bh_graph_create(self.sc.handle, self.cams, self.wv, self.hv, self.dirs,
+                                            self.flags, self.rgba, self.opts)
+
+    def render(self):
+        if self.graph:
+            self.bh.bh_graph_launch(self.graph, self.stream)
+        else:
+            self.bh.bh_render(self.sc.handle, self.cams, self.wv, self.hv, self.dirs, self.flags,
+                              self.rgba, self.opts)
+
+    def timed(self, steps, warmup, flush, barrier=None):
+        """Warm-up renders, then `steps` renders each bracketed by CUDA events
+        on the render stream (L2 flushed before each, outside the events).
+        Returns (total ms, per-render kernel times, statistics summed)."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                self.render()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        kernel_ms, tot = [], {}
+        if barrier:
+            barrier()
+        for k in range(steps):
+            with torch.cuda.stream(self.stream):
+                flush.fill_(k & 255)
+                starts[k].record(self.stream)
+                self.render()
+                ends[k].record(self.stream)
+            st = self.bh.bh_render_stats(self.sc.handle)  # syncs the stream, outside the events
+            kernel_ms.append(st["kernel_ms"])
+            for key in ("steps", "steps_fp64", "mlp_rays", "n_surrogate"):
+                tot[key] = tot.get(key, 0) + st[key]
+        if barrier:
+            barrier()
+        self.bh.bh_scene_sync(self.sc.handle)
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return ms, kernel_ms, tot
+
+    def roofline(self, kernel_ms, tot, steps, peaks):
+        """Roofline of the dominant kernel: the integrator (coherent +
+        long-ray passes) against the FP32 pipe (FP64 pipe in the FP64 form),
+        or the surrogate pass against the special-function unit that one
+        tanh per hidden activation loads, with its tensor-pipe work beside."""
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        if self.form == "surrogate":
+            t_ms = sum(km[0] for km in kernel_ms)
+            mufu = tot["mlp_rays"] * MLP_MUFU_PER_RAY
+            peak = SM_COUNT * MUFU_PER_SM * sm_max * 1e6 / 1e12
+            achieved = mufu / (t_ms * 1e-3) / 1e12 if t_ms > 0 else None
+            flops = tot["mlp_rays"] * MLP_FLOP_PER_RAY / (t_ms * 1e-3) / 1e12 if t_ms > 0 else None
+            bf16 = peaks.get("bf16_tflops")
+            return {
+                "bound": "xu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "k_surrogate (MLP by mma.sync BF16 + integrator fallback)",
+                "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM} MUFU ops per cycle x "
+                               f"{sm_max:.0f} MHz (max SM clock)",
+                "algorithmic": f"{MLP_MUFU_PER_RAY} tanh per network evaluation x "
+                               f"{tot['mlp_rays'] / steps:.0f} evaluations per frame",
+                "tensor": {"achieved": flops, "peak": bf16, "unit": "TFLOP/s",
+                           "frac": flops / bf16 if (flops and bf16) else None,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst) of measured",
+                           "algorithmic": f"{MLP_FLOP_PER_RAY} FLOP per evaluated ray"},
+                "surrogate_pass_ms": t_ms / steps,
+            }
+        int_ms = sum(km[0] + km[1] for km in kernel_ms)
+        lanes = FP64_LANES_PER_SM if self.f64 else FP32_LANES_PER_SM
+        peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
+        n_steps = tot["steps"] if self.f64 else tot["steps"] - tot["steps_fp64"]
+        flop_step = FLOP_PER_RK4_STEP if self.paper else FLOP_PER_STEP
+        achieved = n_steps * flop_step / (int_ms * 1e-3) / 1e12 if int_ms > 0 else None
+        prec = "FP64" if self.f64 else "FP32"
+        return {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved is not None else None, "traffic": None,
+            "kernel": ("k_paper" if self.paper else "k_coherent + k_longrays") + f" ({prec} steps)",
+            "peak_source": f"derived: {SM_COUNT} SMs x {lanes} {prec} FMA lanes x 2 FLOP x "
+                           f"{sm_max:.0f} MHz (max SM clock)",
+            "algorithmic": f"{flop_step} FLOP per attempted {prec} step x "
+                           f"{n_steps / steps:.0f} steps per frame",
+            "integrator_ms_per_step": int_ms / steps,
+        }
+
+    def close(self):
+        if self.graph:
+            self.bh.bh_graph_destroy(self.graph)
+            self.graph = None
+        self.bh.bh_autotune_reset()
+        self.sc.close()
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -279,155 +446,112 @@ def run_ours(args) -> None:
             dist.all_reduce(t)
         torch.cuda.synchronize()
 
-    w = workload(args.form, args.size, args.workload)
-    if args.sky_image:
-        from dataclasses import replace
-        w = replace(w, scene=replace(w.scene, sky_texture=W.sky_texture(0, 2048, 1024)))
-    n = w.n_rays
-    sc = bh.Scene(w.scene)
-    cams = sc.cameras(w.cameras)
-    wv = [c.w for c in w.cameras]
-    hv = [c.h for c in w.cameras]
     stream = torch.cuda.Stream()
-    f64 = args.form in ("fp64", "paper")
-    paper = args.form in ("paper", "paper_fp32")
-    dirs = torch.empty(2 * n, dtype=torch.float64 if f64 else torch.float32, device="cuda")
-    flags = torch.empty(n, dtype=torch.int16, device="cuda")
-    rgba = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-    opts = bh.render_opts(args.form, stream, rtol=w.rtol, atol=w.atol, band=w.band,
-                          paper_eps=args.paper_eps, spp=args.spp, doppler=int(args.doppler))
-    # rays traced per pixel: n x n samples plus the centre ray when anti-aliased
-    rays_per_pixel = args.spp + 1 if args.spp > 1 else 1
-
-    surrogate = None
-    if args.form == "surrogate":
-        # trained weights of the project (train_surrogate.py); training time
-        # is reported separately and is not part of the timed region
-        path = os.path.join(ROOT, "paper_2507_16165_gb300", "data", "surrogate_m1.bin")
-        bh.bh_surrogate_load(sc.handle, path)
-        try:
-            with open(os.path.splitext(path)[0] + ".json") as f:
-                surrogate = json.load(f)
-        except OSError:
-            surrogate = {"weights": path}
-    graph = None
-    tuned = None
-    if args.workload == "c5":
-        # autotune the launch shape on this workload, then capture the whole
-        # multi-camera render once and replay it
-        tuned = bh.bh_autotune(sc.handle, cams, wv, hv, dirs, flags, rgba, opts)
-        graph = bh.bh_graph_create(sc.handle, cams, wv, hv, dirs, flags, rgba, opts)
-
-    def render():
-        if graph:
-            bh.bh_graph_launch(graph, stream)
-        else:
-            bh.bh_render(sc.handle, cams, wv, hv, dirs, flags, rgba, opts)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            render()
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kernel_ms, steps32, steps_all = [], 0, 0
-    barrier()
+    peaks = measured_peaks()
+    extra = {"periastron_reset": 2} if args.periastron_reset == 2 else {}
+    fr = FormRun(bh, torch, args.form, args.workload, args.size, extra, stream, args)
+    w, n = fr.w, fr.n
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 255)                 # L2 flush, outside the events
-                starts[k].record(stream)
-                render()
-                ends[k].record(stream)
-            st = bh.bh_render_stats(sc.handle)       # syncs the stream, outside the events
-            kernel_ms.append(st["kernel_ms"])
-            steps_all += st["steps"]
-            steps32 += st["steps"] - st["steps_fp64"]
-        barrier()
+        ms, kernel_ms, tot = fr.timed(args.steps, args.warmup, flush, barrier)
         t_wall = time.perf_counter() - t_wall
-    bh.bh_scene_sync(sc.handle)
-    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, "cuda")
+    ms = max_over_ranks(ms, world, "cuda")
     ms_per_step = ms / args.steps
-    value = job_rate(n * rays_per_pixel, args.steps, world, ms * 1e-3)
-
-    # roofline: the integrator kernels (coherent + long-ray passes) against
-    # the FP32 pipe, or the FP64 pipe in the FP64 form
-    int_ms = sum(km[0] + km[1] for km in kernel_ms)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    lanes = FP64_LANES_PER_SM if f64 else FP32_LANES_PER_SM
-    peak_tflops = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
-    n_steps = steps_all if f64 else steps32
-    flop_step = FLOP_PER_RK4_STEP if paper else FLOP_PER_STEP
-    achieved = n_steps * flop_step / (int_ms * 1e-3) / 1e12 if int_ms > 0 else None
-    prec = "FP64" if f64 else "FP32"
-    method = f"fixed-step Runge-Kutta 4, eps {args.paper_eps}" if paper else "Dormand-Prince"
-    roofline = {
-        "bound": "alu",
-        "achieved": achieved,
-        "peak": peak_tflops,
-        "unit": "TFLOP/s",
-        "frac": (achieved / peak_tflops) if achieved is not None else None,
-        # DRAM bytes per launch from the ncu capture of this exact workload
-        # (the 4096^2 config-3 frame, default shading, one sample per pixel)
-        "traffic": profile_traffic(args.form) if (args.workload == "c3" and args.size == 4096
-                                                  and args.spp <= 1 and not args.sky_image
-                                                  and not args.doppler) else None,
-        "kernel": ("k_paper" if paper else "k_coherent + k_longrays") + f" ({prec} {method} steps)",
-        "peak_source": f"derived: {SM_COUNT} SMs x {lanes} {prec} FMA lanes x 2 FLOP x "
-                       f"{sm_max:.0f} MHz (max SM clock)",
-        "algorithmic": f"{flop_step} FLOP per attempted {prec} step x "
-                       f"{n_steps / args.steps:.0f} steps per frame",
-        "integrator_ms_per_step": int_ms / args.steps,
-    }
+    value = job_rate(n * fr.rays_per_pixel, args.steps, world, ms * 1e-3)
+    roofline = fr.roofline(kernel_ms, tot, args.steps, peaks)
+    # DRAM bytes per launch from the ncu capture of this exact workload
+    # (the 4096^2 config-3 frame, default shading, one sample per pixel)
+    if (args.workload == "c3" and args.size == 4096 and args.spp <= 1 and not args.sky_image
+            and not args.doppler and not extra):
+        roofline["traffic"] = profile_traffic(args.form)
 
     # end to end through the C-ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
-        hd = torch.empty(2 * n, dtype=dirs.dtype, pin_memory=True)
+        hd = torch.empty(2 * n, dtype=fr.dirs.dtype, pin_memory=True)
         hf = torch.empty(n, dtype=torch.int16, pin_memory=True)
         hr = torch.empty(n, dtype=torch.int32, pin_memory=True)
         for _ in range(max(1, args.warmup)):
-            bh.bh_render_host(sc.handle, cams, wv, hv, hd, hf, hr, opts)
+            bh.bh_render_host(fr.sc.handle, fr.cams, fr.wv, fr.hv, hd, hf, hr, fr.opts)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            bh.bh_render_host(sc.handle, cams, wv, hv, hd, hf, hr, opts)
+            bh.bh_render_host(fr.sc.handle, fr.cams, fr.wv, fr.hv, hd, hf, hr, fr.opts)
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         import ctypes
         from paper_2507_16165_gb300 import _capi
-        e2e = {"value": job_rate(n * rays_per_pixel, args.steps, world, dt), "unit": UNIT,
-               "h2d_bytes_per_step": len(cams) * (ctypes.sizeof(_capi.bh_camera) + 8),
-               "d2h_bytes_per_step": n * (dirs.element_size() * 2 + 2 + 4)}
+        e2e = {"value": job_rate(n * fr.rays_per_pixel, args.steps, world, dt), "unit": UNIT,
+               "h2d_bytes_per_step": len(fr.cams) * (ctypes.sizeof(_capi.bh_camera) + 8),
+               "d2h_bytes_per_step": n * (fr.dirs.element_size() * 2 + 2 + 4)}
 
-    stats = bh.bh_render_stats(sc.handle)
-    if graph:
-        bh.bh_graph_destroy(graph)
-    sc.close()
+    stats = bh.bh_render_stats(fr.sc.handle)
+    tuned, surrogate = fr.tuned, fr.surrogate
+    fr.close()
+
+    # every form of the metric, each on its own workload, after the headline
+    forms = None
+    if not args.no_forms:
+        forms = {}
+        with ClockSampler(local) as fclk:
+            for name, (form, wname, fextra, test) in FORMS.items():
+                f = FormRun(bh, torch, form, wname, 4096, fextra, stream, args)
+                k = 3 if form == "fp64" else max(3, min(args.steps, 10))
+                fms, fkm, ftot = f.timed(k, 3, flush, barrier)
+                fms = max_over_ranks(fms, world, "cuda")
+                forms[name] = {
+                    "workload": f.w.name, "rays_per_frame": f.n,
+                    "mrays_per_s": job_rate(f.n, k, world, fms * 1e-3),
+                    "ms_per_frame": fms / k, "steps": k,
+                    "steps_per_ray": ftot["steps"] / k / f.n,
+                    "stated_exit_dir_error_rad": STATED_ERROR[form],
+                    "error_asserted_by": test,
+                    "options": fextra or None,
+                    "roofline": f.roofline(fkm, ftot, k, peaks),
+                    "launch": ("autotuned shape in one CUDA-graph replay: " + json.dumps(f.tuned))
+                    if f.tuned else "bh_render, default launch shape",
+                    "served_fraction": ftot["n_surrogate"] / k / f.n if form == "surrogate" else None,
+                }
+                f.close()
+        base = forms["fp64"]["mrays_per_s"]
+        for name, e in forms.items():
+            e["speedup_vs_fp64_gpu"] = e["mrays_per_s"] / base if name.startswith(("fp", "mixed", "surr")) else None
+        forms["clocks"] = fclk.summary()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     cpu = None if (args.no_cpu or world > 1 or args.workload != "c3") else \
         cpu_baseline(w, args.cpu_seconds)
+    c5 = args.workload == "c5"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else ("f32" if paper else "f32+f64"),
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fr.f64 else ("f32" if (fr.paper or args.form == "fp32") else "f32+f64"),
         "data": "synthetic",
         "config": {"workload": w.name, "form": args.form, "rays_per_step": n,
-                   "size": (f"{args.size}x{args.size}" if args.workload == "c3"
-                            else f"{len(w.cameras)} cameras, 256^2..2048^2"),
-                   "r_obs": 50.0 if args.workload == "c3" else "15..100 (log-uniform)",
-                   "inclination_deg": 75.0 if args.workload == "c3" else "0..89",
+                   "size": (f"{len(w.cameras)} cameras, 256^2..2048^2" if c5
+                            else f"{args.size}x{args.size}"),
+                   "r_obs": "15..100 (log-uniform)" if c5 else 50.0,
+                   "inclination_deg": "0..89" if c5 else 75.0,
                    "disk": list(w.scene.disk), "spheres": len(w.scene.spheres),
-                   "rtol": w.rtol, "atol": w.atol,
-                   "band": w.band, "stated_exit_dir_error_rad": STATED_ERROR[args.form],
-                   "paper_eps": args.paper_eps if paper else None,
+                   "rtol": fr.opts.rtol, "atol": fr.opts.atol,
+                   "rtol_far": 10 * fr.opts.rtol if not fr.f64 else fr.opts.rtol,
+                   "h_max": 0.3 if not fr.f64 else None,
+                   "h_max_far": 0.5 if not fr.f64 else None,
+                   "far_rays": "|b - 3 sqrt(3) M| >= 2M take rtol_far and h_max_far",
+                   "band": w.band,
+                   "band_rtol": 1e-8 if args.form in ("mixed", "surrogate") else None,
+                   "periastron_reset": (("FP64 turning point for every ray (b from the FP64 image "
+                                         "radius)" if extra else
+                                         "FP64 turning point for |b - 3 sqrt(3) M| < 2M")
+                                        if args.form in ("mixed", "surrogate") else None),
+                   "rtol_near": (fr.opts.rtol / 100 if args.form == "fp32" else None),
+                   "stated_exit_dir_error_rad": STATED_ERROR[args.form],
+                   "paper_eps": args.paper_eps if fr.paper else None,
                    "spp": args.spp if args.spp > 1 else None,
                    "disk_shading": "keplerian doppler" if args.doppler else "temperature ramp",
                    "sky": "2048x1024 image, bilinear" if args.sky_image else "procedural checker",
@@ -441,6 +565,7 @@ def run_ours(args) -> None:
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_RENDER[args.form] * args.steps,
         "clocks": clk.summary(),
+        "forms": forms,
         "surrogate_training": (dict({k: surrogate.get(k) for k in
                                      ("samples", "n_valid", "epochs", "steps", "wall_s",
                                       "train_ms", "label_ms", "val_rmse")},
@@ -449,11 +574,11 @@ def run_ours(args) -> None:
                                     served_bins=surrogate["calibration"]["served_bins"],
                                     served_rays_fraction=stats["n_surrogate"] / n)
                                if surrogate else None),
-        "steps_per_ray": steps_all / args.steps / (n * rays_per_pixel),
+        "steps_per_ray": tot["steps"] / args.steps / (n * fr.rays_per_pixel),
         "wall_s": t_wall,
         "stats_last": {k: stats[k] for k in ("rays", "n_band", "n_long", "periastron", "n_capt",
                                              "n_disk", "n_sphere", "n_esc", "n_surrogate",
-                                             "n_fallback")},
+                                             "n_fallback", "mlp_rays")},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -463,7 +588,7 @@ def run_ours(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("mixed", "fp32", "fp64", "surrogate", "paper", "paper_fp32"),
@@ -479,6 +604,10 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--workload", choices=("c3", "c5"), default="c3")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other forms of the metric (measured after the headline)")
+    ap.add_argument("--periastron-reset", type=int, default=1, choices=(1, 2),
+                    help="mixed form: FP64 turning point for near-critical rays (1) or all (2)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pixels", type=int, default=1 << 18)

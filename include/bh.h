@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define BH_ABI_VERSION 1
+#define BH_ABI_VERSION 2
 #define BH_MAX_SPHERES 8
 
 /* ---- return codes ---------------------------------------------------- */
@@ -120,7 +120,11 @@ typedef struct bh_scene_desc {
 } bh_scene_desc;
 
 /* Pinhole camera.  bh_camera_set fills every field from the four angles;
- * the derived basis is what the kernels read. */
+ * the derived basis is what the kernels read.  The renderers accept only
+ * cameras that look at the hole (fwd = -pos / r_obs, right and up an
+ * orthonormal basis perpendicular to it, to 1e-9), as bh_camera_set makes
+ * them: the kernels reduce each ray to its orbital plane from its image-plane
+ * coordinates (Sec. 2.2: the camera's line of sight through the hole). */
 typedef struct bh_camera {
   double r_obs, incl_deg, azim_deg, fov_deg;
   double pos[3];   /* r_obs (sin i cos a, sin i sin a, cos i)              */
@@ -142,9 +146,12 @@ typedef struct bh_render_opts {
                          the quintic event interpolant needs short steps)   */
   void *stream;       /* cudaStream_t                                       */
   /* launch shape; 0 selects the tuned value for this device and mode      */
-  int block_size;     /* threads per block: 64, 128 or 256                  */
+  int block_size;     /* threads per block: 64, 128, 256 or 512             */
   int blocks_per_sm;  /* resident blocks per SM in the persistent grid      */
-  int tile_w, tile_h; /* pixel tile that one warp takes (tile_w*tile_h = 32)*/
+  int tile_w, tile_h; /* pixel tile of the work queue: tile_w * tile_h a
+                         power of two in [32, 256], tile_w a power of two;
+                         its pixels are queued row-major, and a warp takes
+                         them 32 at a time                                 */
   int budget;         /* steps a ray may take in the coherent pass before it
                          moves to the long-ray queue                        */
   int periastron_reset; /* MIXED: reset the state at the turning point from
@@ -182,6 +189,14 @@ typedef struct bh_render_opts {
                          while the next renders (0: about 2^21 rays a strip;
                          at most BH_MAX_HOST_STRIPS; the surrogate renders
                          whole)                                             */
+  double rtol_near;   /* BH_MODE_FP32: rtol of rays with |b - 3 sqrt(3) M| <
+                         band (their atol scales with it); their capture
+                         decision and exit direction depend on the first
+                         integral to a few parts in 1e6 (0: rtol / 100; the
+                         other modes integrate those rays in FP64)          */
+  int queue_chunk;    /* queue slots (rays) a warp takes per grab of the
+                         global work counter, a multiple of 32 in [32, 1024];
+                         0: the tuned value                                 */
 } bh_render_opts;
 
 typedef struct bh_stats {
@@ -198,12 +213,18 @@ typedef struct bh_stats {
   uint64_t events;        /* event-handling passes (nodes, windows, roots)   */
   uint64_t steps_fp64;    /* attempted steps taken in FP64 (part of steps)   */
   uint32_t status;        /* BH_STATUS_* bits of the last render             */
-  float kernel_ms[4];     /* device time of the last render: [0] coherent pass
-                             (MIXED: with the band list and the FP64 band
-                             pass, which runs beside it), [1] long-ray pass,
-                             [2] FP64 band pass of the surrogate mode (on a
-                             side stream beside [0] and [1]; 0 otherwise),
-                             [3] whole render                               */
+  float kernel_ms[4];     /* device time of the last render: [0] the tile pass
+                             and the long-ray pass, which starts as its
+                             programmatic dependent (MIXED: with the band
+                             list and the FP64 band pass, which runs beside
+                             them; SURROGATE: the band list and the
+                             surrogate pass), [1] the surrogate mode's
+                             integrator pass over the rays the network does
+                             not answer (0 otherwise), [2] FP64 band pass
+                             of the surrogate mode (on a side stream beside
+                             [0] and [1]; 0 otherwise), [3] whole render   */
+  uint64_t mlp_rays;      /* rays the surrogate network was evaluated for:
+                             32 per warp that had a ray to serve            */
 } bh_stats;
 
 /* Library version (BH_ABI_VERSION). */
@@ -402,6 +423,7 @@ typedef struct bh_tune_result {
   float ms_best;     /* its render time                                   */
   float ms_default;  /* render time with the built-in default shape        */
   int trials;        /* shapes timed                                       */
+  int queue_chunk;   /* queue slots per warp grab of the fastest shape     */
 } bh_tune_result;
 
 /* Time candidate launch shapes (block size, tile shape, step budget and, in
@@ -426,14 +448,20 @@ int bh_autotune_reset(void);
  * BH_E_UNSUPPORTED) but allocates nothing and needs no bh_scene: the scene
  * is read from desc on every call, and the only scratch -- the work-queue
  * counter, status and statistics words and the camera table -- lives in one
- * fixed library-owned device array of about 10 KB, present on every device
+ * fixed library-owned device array of about 48 KB, present on every device
  * that loads the library until the process exits.  Every ray is finished by
- * the coherent pass (no long-ray list), so results equal bh_render's.
+ * the coherent pass (no long-ray list) with the kernels bh_render uses, so
+ * the outputs equal bh_render's for the same options.
  *   - desc, cams, w, h: host, as for bh_scene_create / bh_render;
  *     n_cams <= BH_NOALLOC_MAX_CAMERAS, else BH_E_INVALID.
  *   - out_dirs, out_flags, out_rgba8: caller-owned device buffers laid out
  *     as for bh_render.
- *   - Asynchronous on opts->stream; the camera table is copied on it.
+ *   - Asynchronous on opts->stream.  The camera table reaches the scratch
+ *     array in the launch parameters of a copy kernel on that stream, so no
+ *     device work of the call reads the caller's host memory after it
+ *     returns.
+ *   - opts->abort_after must be 0 (BH_E_UNSUPPORTED otherwise): this entry
+ *     point reads no device status back.
  *   - The first call on a device looks up the scratch array's device
  *     address (with that device current); make that first call before any
  *     stream capture.

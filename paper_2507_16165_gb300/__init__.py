@@ -321,8 +321,8 @@ def bh_scene_sync(scene: int) -> None:
 def bh_render_stats(scene: int) -> dict:
     st = _capi.bh_stats()
     check(_capi.lib().bh_render_stats(scene, ctypes.byref(st)), "bh_render_stats")
-    out = {name: int(getattr(st, name)) for name, _ in _capi.bh_stats._fields_[:-2]}
-    out["status"] = int(st.status)
+    out = {name: int(getattr(st, name)) for name, _ in _capi.bh_stats._fields_
+           if name != "kernel_ms"}
     out["kernel_ms"] = [float(x) for x in st.kernel_ms]
     return out
 

@@ -61,7 +61,8 @@ class bh_render_opts(ctypes.Structure):
                 ("periastron_reset", ctypes.c_int), ("abort_after", ctypes.c_uint32),
                 ("h_max_far", ctypes.c_double), ("paper_eps", ctypes.c_double),
                 ("spp", ctypes.c_int), ("doppler", ctypes.c_int),
-                ("rtol_far", ctypes.c_double), ("host_strips", ctypes.c_int)]
+                ("rtol_far", ctypes.c_double), ("host_strips", ctypes.c_int),
+                ("rtol_near", ctypes.c_double), ("queue_chunk", ctypes.c_int)]
 
 
 class bh_stats(ctypes.Structure):
@@ -69,7 +70,8 @@ class bh_stats(ctypes.Structure):
         "rays", "steps", "rejected", "n_esc", "n_capt", "n_disk", "n_sphere", "n_step_limit",
         "n_band", "n_long", "n_surrogate", "n_fallback", "queue_grabs", "periastron",
         "events", "steps_fp64")] + [("status", ctypes.c_uint32),
-                                    ("kernel_ms", ctypes.c_float * 4)]
+                                    ("kernel_ms", ctypes.c_float * 4),
+                                    ("mlp_rays", ctypes.c_uint64)]
 
 
 class bh_train_opts(ctypes.Structure):
@@ -100,7 +102,7 @@ class bh_tune_result(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("ms_best", ctypes.c_float), ("ms_default", ctypes.c_float),
-                ("trials", ctypes.c_int)]
+                ("trials", ctypes.c_int), ("queue_chunk", ctypes.c_int)]
 
 
 _lock = threading.Lock()

@@ -26,9 +26,14 @@ struct SceneR {
   // rounding of b; +inf when that is not above 3 sqrt(3) M (a sphere
   // reaching inside about 3M, which captured orbits may meet).
   R cull_b[kMaxSph];
+  R cnorm[kMaxSph];  // |c_k|
 };
 
-// Camera constants in the kernel's arithmetic type.
+// Camera constants in the kernel's arithmetic type.  A camera looks at the
+// hole (fwd = -pos / r_obs), so the ray through image-plane point (sx, sy)
+// has tan(alpha) = rho = |(sx, sy)| with alpha its angle from the direction
+// of the hole, its orbital plane holds e1 = pos / r_obs and
+// e2 = (sx right + sy up) / rho, and its normal is n = (sx up - sy right) / rho.
 template <typename R>
 struct CamR {
   R pos[3], fwd[3], right[3], up[3];
@@ -37,6 +42,12 @@ struct CamR {
   R px_scale;        // 2 sx / w: image-plane step per pixel column
   R py_scale;        // 2 sy / h
   R inv_tiles_x;     // 1 / tiles_x (a first guess for the tile row)
+  R pdiag;           // sqrt(px_scale^2 + py_scale^2): one pixel's diagonal
+  R kb;              // b = kb sin(alpha): r_obs / sqrt(1 - 2M / r_obs) (static observer)
+  R kv;              // u'0 = kv / rho: u0 sqrt(1 - 2M u0) (static) or u0 (Euclidean)
+  R ec[kMaxSph];     // e1 . c_k
+  R rc[kMaxSph];     // right . c_k
+  R uc[kMaxSph];     // up . c_k
 };
 
 // Tolerances and caps in the kernel's arithmetic type.
@@ -45,11 +56,24 @@ struct TolR {
   R rtol, atol, phi_max, h_max, band;
   R h_far;  // step cap of rays with |b - b_c| >= kFarB (FP32 passes)
   R far_e2; // (rtol / rtol_far)^2: their squared error norm is scaled by it
+  R near_e2; // FP32 form: (rtol / rtol_near)^2 for rays with |b - b_c| < band
 };
 
 // Rays at least this far from the critical impact parameter (units of M)
 // take the relaxed step cap h_far and tolerance rtol_far in the FP32 passes.
 constexpr double kFarB = 2.0;
+
+// Tile shapes: tile_w * tile_h slots, a power of two from 32 to 256, tile_w
+// a power of two.
+inline bool tile_shape_ok(int tw, int th) {
+  const int t = tw * th;
+  return tw >= 1 && th >= 1 && t >= 32 && t <= 256 && (t & (t - 1)) == 0 && (tw & (tw - 1)) == 0;
+}
+inline int ilog2(int x) {
+  int k = 0;
+  while ((1 << (k + 1)) <= x) ++k;
+  return k;
+}
 
 // Scene constants, passed by value in every kernel's parameter block.
 struct SceneK {
@@ -75,8 +99,9 @@ struct SceneK {
 };
 
 // One camera in device memory.  Its rays occupy queue slots
-// [q_off, q_off + tiles_x * tiles_y * 32): one 32-ray tile per warp grab,
-// padded where w or h is not a multiple of the tile.
+// [q_off, q_off + tiles_x * tiles_y * tile_w * tile_h): tile after tile,
+// row-major within a tile, padded where w or h is not a multiple of the
+// tile; a warp takes its 32-slot groups in turn.
 struct CamK {
   double pos[3], fwd[3], right[3], up[3];
   double sx, sy;       // tan(fov/2) and tan(fov/2) * h / w
@@ -91,6 +116,9 @@ struct CamK {
   float peri_k0f;
   // MIXED band as bounds on the squared image-plane radius (band_pixel)
   float band_rho2_lo, band_rho2_hi;
+  // 1/b^2 of the ray through image-plane radius rho: peri_A + peri_B / rho^2
+  // (FP64, u0 = 1/r_obs; MIXED turning point with periastron_reset = 2)
+  double peri_A, peri_B;
   int row_off;  // first row of this camera among all cameras' rows
 };
 
@@ -107,6 +135,11 @@ inline double band_rho2_of_b(double b, double r, double M, int ic) {
 }
 inline void fill_cam_band(CamK& c, double M, int ic, double band) {
   const double bc = 3.0 * std::sqrt(3.0) * M;
+  // 1/b^2 = u0^2 (1 - 2M u0) / sin^2(alpha) (static observer) or
+  // u0^2 / sin^2(alpha) - 2M u0^3 (Euclidean), with 1/sin^2 = 1 + 1/rho^2
+  const double u0 = 1.0 / c.r_obs;
+  c.peri_A = u0 * u0 * (1.0 - 2.0 * M * u0);
+  c.peri_B = ic == 0 ? c.peri_A : u0 * u0;
   if (!(band > 0.0) || !(M > 0.0)) {
     c.band_rho2_lo = c.band_rho2_hi = -1.0f;
     return;
@@ -124,7 +157,7 @@ inline void fill_cam_peri(CamK& c, float M) {
 
 enum StatId {
   ST_RAYS, ST_STEPS, ST_REJ, ST_ESC, ST_CAPT, ST_DISK, ST_SPH, ST_LIM, ST_BAND, ST_LONG,
-  ST_SURR, ST_FALLBACK, ST_GRABS, ST_PERI, ST_EVENTS, ST_STEPS64, ST_N
+  ST_SURR, ST_FALLBACK, ST_GRABS, ST_PERI, ST_EVENTS, ST_STEPS64, ST_MLP, ST_N
 };
 
 // Device workspace: queue counters, list lengths, status and statistics.
@@ -161,6 +194,9 @@ struct Params {
   const CamK* cams;
   int n_cams;
   int tile_w, tile_h;
+  int tile_shift;     // log2(tile_w * tile_h): slots per tile, a power of two >= 32
+  int tile_wshift;    // log2(tile_w)
+  int chunk;          // queue slots a warp takes per grab (a multiple of 32)
   int budget;
   long long n_queue;  // queue slots: the pass takes slots [q_begin, n_queue)
   long long q_begin;  // first slot (0; a later window when a render is split into strips)
@@ -172,6 +208,7 @@ struct Params {
   double h_max;                 // step-size cap of the main pass (FP64 band: none)
   double h_max_far;             // FP32 step cap of rays with |b - b_c| >= kFarB
   double rtol_far;              // FP32 rtol of those rays (atol scaled alike)
+  double rtol_near;             // FP32 form: rtol of rays with |b - b_c| < band
   double paper_eps;             // fixed step of the polyline modes
   int spp_n;                    // samples per pixel side (n x n), 1 = one centre ray
   int doppler;                  // Keplerian disk shading
@@ -217,12 +254,15 @@ inline void fill_scene_r(const SceneK& s, SceneR<R>* o) {
     o->c2[k] = R(s.c2[k]);
     o->rad[k] = R(s.R[k]);
     o->K[k] = R(s.K[k]);
+    o->cnorm[k] = R(std::sqrt(s.c2[k]));
     const double cb = (std::sqrt(s.c2[k]) + s.R[k]) * (1.0 + 1e-5) + 2.25 * s.M;
     o->cull_b[k] = cb > 1.001 * s.b_crit ? R(cb) : R(INFINITY);
   }
 }
+// Typed camera constants; the scene gives the mass, the initial-condition
+// convention and the sphere centres.
 template <typename R>
-inline void fill_cam_r(const CamK& c, CamR<R>* o) {
+inline void fill_cam_r(const CamK& c, const SceneK& s, CamR<R>* o) {
   for (int j = 0; j < 3; ++j) {
     o->pos[j] = R(c.pos[j]);
     o->fwd[j] = R(c.fwd[j]);
@@ -233,9 +273,25 @@ inline void fill_cam_r(const CamK& c, CamR<R>* o) {
   o->sy = R(c.sy);
   o->r_obs = R(c.r_obs);
   o->ir = R(1.0 / c.r_obs);
-  o->px_scale = R(2.0 * c.sx / c.w);
-  o->py_scale = R(2.0 * c.sy / c.h);
+  const double pxs = 2.0 * c.sx / c.w, pys = 2.0 * c.sy / c.h;
+  o->px_scale = R(pxs);
+  o->py_scale = R(pys);
   o->inv_tiles_x = R(1.0 / c.tiles_x);
+  o->pdiag = R(std::sqrt(pxs * pxs + pys * pys));
+  const double u0 = 1.0 / c.r_obs;
+  o->kb = R(c.r_obs / std::sqrt(1.0 - 2.0 * s.M * u0));
+  o->kv = R(s.ic == 0 ? u0 * std::sqrt(1.0 - 2.0 * s.M * u0) : u0);
+  for (int k = 0; k < kMaxSph; ++k) {
+    double e = 0.0, rr = 0.0, uu = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      e += c.pos[j] * u0 * s.c[k][j];
+      rr += c.right[j] * s.c[k][j];
+      uu += c.up[j] * s.c[k][j];
+    }
+    o->ec[k] = R(e);
+    o->rc[k] = R(rr);
+    o->uc[k] = R(uu);
+  }
 }
 
 }  // namespace bhk

@@ -38,6 +38,17 @@ int bh_cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" int bh_version(void) { return BH_ABI_VERSION; }
 
+bool camera_looks_at_hole(const bh_camera& c) {
+  auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+  if (!(c.r_obs > 0.0)) return false;
+  const double tol = 1e-9;
+  for (int k = 0; k < 3; ++k)
+    if (!(std::fabs(c.fwd[k] + c.pos[k] / c.r_obs) <= tol)) return false;
+  return std::fabs(dot(c.fwd, c.fwd) - 1.0) <= tol && std::fabs(dot(c.right, c.right) - 1.0) <= tol &&
+         std::fabs(dot(c.up, c.up) - 1.0) <= tol && std::fabs(dot(c.fwd, c.right)) <= tol &&
+         std::fabs(dot(c.fwd, c.up)) <= tol && std::fabs(dot(c.right, c.up)) <= tol;
+}
+
 extern "C" const char* bh_last_error(void) { return g_last_error.c_str(); }
 
 // ---------------------------------------------------------------------------
@@ -267,15 +278,22 @@ int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, con
     if (!(cams[i].r_obs > 2.0 * sc->sk.M) || !(cams[i].tan_half > 0.0) ||
         !std::isfinite(cams[i].tan_half))
       return bh_fail(BH_E_INVALID, "bh_render: camera %d not set (bh_camera_set) or inside r = 2M", i);
+    if (!camera_looks_at_hole(cams[i]))
+      return bh_fail(BH_E_INVALID,
+                     "bh_render: camera %d must look at the hole with an orthonormal basis (bh_camera_set)", i);
   }
   const int tw = opts->tile_w, th = opts->tile_h;
-  if ((tw || th) && (tw < 1 || th < 1 || tw * th != 32))
-    return bh_fail(BH_E_INVALID, "bh_render: tile_w * tile_h must be 32");
+  if ((tw || th) && !tile_shape_ok(tw, th))
+    return bh_fail(BH_E_INVALID,
+                   "bh_render: tile_w * tile_h must be a power of two in [32, 256], tile_w a power of two");
   if (opts->block_size && opts->block_size != 64 && opts->block_size != 128 &&
-      opts->block_size != 256)
-    return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128 or 256");
+      opts->block_size != 256 && opts->block_size != 512)
+    return bh_fail(BH_E_INVALID, "bh_render: block_size must be 64, 128, 256 or 512");
+  if (opts->queue_chunk && (opts->queue_chunk < 32 || opts->queue_chunk > 1024 || opts->queue_chunk % 32))
+    return bh_fail(BH_E_INVALID, "bh_render: queue_chunk must be a multiple of 32 in [32, 1024]");
   if (opts->rtol < 0 || opts->atol < 0 || opts->band < 0 || opts->band_rtol < 0 ||
       opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->paper_eps < 0 || opts->rtol_far < 0 ||
+      opts->rtol_near < 0 ||
       opts->host_strips < 0 || opts->host_strips > BH_MAX_HOST_STRIPS ||
       opts->max_steps < 0 || opts->budget < 0 || opts->blocks_per_sm < 0 || opts->spp < 0)
     return bh_fail(BH_E_INVALID, "bh_render: negative option");
@@ -315,10 +333,10 @@ int build_cameras(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
     c.tiles_y = (h[i] + th - 1) / th;
     c.q_off = q;
     c.out_off = o;
-    fill_cam_r(c, &c.f);
-    fill_cam_r(c, &c.d);
+    fill_cam_r(c, sc->sk, &c.f);
+    fill_cam_r(c, sc->sk, &c.d);
     fill_cam_peri(c, sc->sk.f.M);
-    q += 32LL * c.tiles_x * c.tiles_y;
+    q += (long long)tw * th * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }
   if (q >= 0x7FFFFFFFLL || o >= 0x7FFFFFFFLL)
@@ -340,6 +358,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.h_max = o->h_max > 0 ? o->h_max : (f64 ? INFINITY : 0.3);
   c.h_max_far = o->h_max_far > 0 ? o->h_max_far : (f64 ? c.h_max : 0.5);
   c.rtol_far = o->rtol_far > 0 ? o->rtol_far : (f64 ? c.rtol : 10.0 * c.rtol);
+  c.rtol_near = o->rtol_near > 0 ? o->rtol_near : (f64 ? c.rtol : 0.01 * c.rtol);
   c.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
   c.paper_eps = o->paper_eps > 0 ? o->paper_eps : 0.01;
   c.doppler = o->doppler ? 1 : 0;
@@ -351,6 +370,7 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.tile_w = o->tile_w ? o->tile_w : t.tile_w;
   c.tile_h = o->tile_h ? o->tile_h : t.tile_h;
   c.budget = o->budget ? o->budget : t.budget;
+  c.chunk = o->queue_chunk ? o->queue_chunk : t.chunk;
   if (c.spp_n > 1) c.budget = c.max_steps;  // every sample finishes in the tile pass
   c.band_lanes = t.band_lanes;
   c.band_warps = t.band_warps;
@@ -409,6 +429,7 @@ int prepare_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w
 // Work of one prepared render on `stream`: clear the workspace, launch the
 // passes.  Also what a CUDA graph of the render captures.
 int enqueue_render(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream) {
+  if (pr.mode == BH_MODE_SURROGATE) return surrogate_enqueue(sc, pr, stream);
   cudaError_t e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
   if (e == cudaSuccess) e = launch_render(pr.p, pr.kmode, pr.ls, stream, sc->ev);
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render: launch");
@@ -417,10 +438,8 @@ int enqueue_render(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream) 
 
 int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                   void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts) {
-  if (opts->mode == BH_MODE_SURROGATE) {
-    const RenderConfig cfg = resolve_config(sc, opts);
-    return surrogate_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, cfg);
-  }
+  if (opts->mode == BH_MODE_SURROGATE)
+    return surrogate_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts);
   cudaStream_t stream = (cudaStream_t)opts->stream;
   PreparedRender pr;
   int rc = prepare_render(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, stream, nullptr, &pr);
@@ -448,6 +467,9 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.n_cams = n_cams;
   p.tile_w = cfg.tile_w;
   p.tile_h = cfg.tile_h;
+  p.tile_shift = ilog2(cfg.tile_w * cfg.tile_h);
+  p.tile_wshift = ilog2(cfg.tile_w);
+  p.chunk = cfg.chunk;
   p.budget = cfg.budget;
   p.n_queue = n_queue;
   p.n_rays = n_rays;
@@ -460,6 +482,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.h_max = cfg.h_max;
   p.h_max_far = cfg.h_max_far;
   p.rtol_far = cfg.rtol_far;
+  p.rtol_near = cfg.rtol_near;
   p.paper_eps = cfg.paper_eps;
   p.spp_n = cfg.spp_n;
   p.doppler = cfg.doppler;
@@ -478,10 +501,11 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
 
 void fill_tolerances(Params& p) {
   const double e = p.rtol_far > 0 ? p.rtol / p.rtol_far : 1.0;
+  const double en = p.rtol_near > 0 ? p.rtol / p.rtol_near : 1.0;
   p.tf = TolR<float>{(float)p.rtol, (float)p.atol, (float)p.phi_max, (float)p.h_max, (float)p.band,
-                     (float)p.h_max_far, (float)(e * e)};
-  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band, p.h_max_far, e * e};
-  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band, INFINITY, 1.0};
+                     (float)p.h_max_far, (float)(e * e), (float)(en * en)};
+  p.td = TolR<double>{p.rtol, p.atol, p.phi_max, p.h_max, p.band, p.h_max_far, e * e, en * en};
+  p.tb = TolR<double>{p.rtol64, p.atol64, p.phi_max, INFINITY, p.band, INFINITY, 1.0, 1.0};
 }
 
 extern "C" int bh_render(const bh_scene* scene, const bh_camera* cams, int n_cams, const int* w,
@@ -503,8 +527,8 @@ struct HostStrip {
 
 // Cut the prepared cameras' tile rows into at most `want` strips of about
 // equal slot counts (want = 0: about 2^21 rays a strip).
-static int cut_strips(const bh_scene* sc, int n_cams, int tile_h, long long n_queue, int want,
-                      HostStrip* out) {
+static int cut_strips(const bh_scene* sc, int n_cams, int tile_w, int tile_h, long long n_queue,
+                      int want, HostStrip* out) {
   if (want <= 0) want = (int)std::min<long long>(BH_MAX_HOST_STRIPS, std::max(1LL, n_queue >> 21));
   const long long target = (n_queue + want - 1) / want;
   int n = 0;
@@ -513,7 +537,7 @@ static int cut_strips(const bh_scene* sc, int n_cams, int tile_h, long long n_qu
     const CamK& c = sc->h_cams[ci];
     for (int ty = 0; ty < c.tiles_y; ++ty) {
       const int y1 = std::min(c.h, (ty + 1) * tile_h);
-      cur.q_hi = c.q_off + (long long)(ty + 1) * c.tiles_x * 32;
+      cur.q_hi = c.q_off + (long long)(ty + 1) * c.tiles_x * tile_w * tile_h;
       cur.o_hi = c.out_off + (long long)y1 * c.w;
       cur.row_hi = c.row_off + y1;
       const bool last = ci == n_cams - 1 && ty == c.tiles_y - 1;
@@ -598,7 +622,8 @@ extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int 
   rc = prepare_render(sc, cams, n_cams, w, h, sd, sf, sr, opts, stream, nullptr, &pr);
   if (rc) return rc;
   HostStrip strips[BH_MAX_HOST_STRIPS];
-  const int ns = cut_strips(sc, n_cams, pr.p.tile_h, pr.p.n_queue, opts->host_strips, strips);
+  const int ns = cut_strips(sc, n_cams, pr.p.tile_w, pr.p.tile_h, pr.p.n_queue, opts->host_strips,
+                            strips);
   const bool mixed = pr.kmode == MODE_MIXED;
   int regs_per_sm = 65536;
   cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, sc->device);
@@ -695,6 +720,7 @@ extern "C" int bh_render_stats(const bh_scene* scene, bh_stats* out) {
   out->periastron = w.stats[ST_PERI];
   out->events = w.stats[ST_EVENTS];
   out->steps_fp64 = w.stats[ST_STEPS64];
+  out->mlp_rays = w.stats[ST_MLP];
   out->status = w.status;
   if (scene->timed) {
     for (int i = 0; i < 2; ++i) {

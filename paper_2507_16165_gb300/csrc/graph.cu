@@ -31,8 +31,6 @@ extern "C" int bh_graph_create(bh_scene* scene, const bh_camera* cams, int n_cam
   *out = nullptr;
   int rc = check_render_args(scene, cams, n_cams, w, h, opts);
   if (rc) return rc;
-  if (opts->mode == BH_MODE_SURROGATE)
-    return bh_fail(BH_E_UNSUPPORTED, "bh_graph_create: integrator modes only");
   DeviceGuard dg(scene->device);
   bh_graph* g = new (std::nothrow) bh_graph();
   if (!g) return bh_fail(BH_E_NOMEM, "bh_graph_create: host allocation");
@@ -46,8 +44,11 @@ extern "C" int bh_graph_create(bh_scene* scene, const bh_camera* cams, int n_cam
     return bh_cuda_fail(e, "bh_graph_create: setup");
   }
   PreparedRender pr;
-  rc = prepare_render(scene, cams, n_cams, w, h, out_dirs, out_flags, out_rgba8, opts, cs,
-                      g->d_cams, &pr);
+  rc = opts->mode == BH_MODE_SURROGATE
+           ? surrogate_prepare(scene, cams, n_cams, w, h, out_dirs, out_flags, out_rgba8, opts, cs,
+                               g->d_cams, &pr)
+           : prepare_render(scene, cams, n_cams, w, h, out_dirs, out_flags, out_rgba8, opts, cs,
+                            g->d_cams, &pr);
   if (!rc) {
     e = cudaStreamSynchronize(cs);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -79,6 +80,8 @@ extern "C" int bh_graph_launch(bh_graph* g, void* stream) {
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_graph_launch");
   g->scene->last_stream = (cudaStream_t)stream;
   g->scene->timed = true;
-  g->scene->band_used = false;
+  // the surrogate's FP64 band pass runs on the scene's side stream, timed
+  // by its own events
+  g->scene->band_used = g->mode == BH_MODE_SURROGATE;
   return BH_OK;
 }

@@ -8,9 +8,12 @@
 // -- in one file-scope __device__ array of fixed size, and runs the coherent
 // pass alone with a step budget equal to the step cap, so no long-ray or
 // band list is needed.  The caller passes the scene description, cameras and
-// output buffers.
+// output buffers.  The camera table reaches the scratch array through the
+// launch parameters of a small copy kernel, so no device work of the call
+// reads host memory after the call has returned.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -32,6 +35,20 @@ constexpr int kMaxDevices = 64;
 // Its name in host code is only a stand-in; kernels get the address that
 // cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Cameras per launch of the copy kernel: 16 camera records (about 6.5 KB)
+// travel in its parameter block.
+constexpr int kCamsPerCopy = 16;
+struct CamChunk {
+  CamK c[kCamsPerCopy];
+  int n;
+};
+
+static_assert(sizeof(CamChunk) <= 32000, "camera chunk must fit a kernel's parameter block");
+
+__global__ void k_noalloc_cams(const __grid_constant__ CamChunk src, CamK* dst) {
+  for (int i = threadIdx.x; i < src.n; i += blockDim.x) dst[i] = src.c[i];
+}
 
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
@@ -118,14 +135,19 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     return bh_fail(BH_E_UNSUPPORTED, "bh_render_noalloc: only BH_MODE_FP32 and BH_MODE_FP64");
   if (opts->spp > 1 || opts->doppler)
     return bh_fail(BH_E_UNSUPPORTED, "bh_render_noalloc: one sample per pixel, plain disk shading only");
-  if ((opts->tile_w || opts->tile_h) &&
-      (opts->tile_w < 1 || opts->tile_h < 1 || opts->tile_w * opts->tile_h != 32))
-    return bh_fail(BH_E_INVALID, "bh_render_noalloc: tile_w * tile_h must be 32");
+  if (opts->abort_after)
+    return bh_fail(BH_E_UNSUPPORTED,
+                   "bh_render_noalloc: abort_after is not available (no status is read back)");
+  if ((opts->tile_w || opts->tile_h) && !tile_shape_ok(opts->tile_w, opts->tile_h))
+    return bh_fail(BH_E_INVALID,
+                   "bh_render_noalloc: tile_w * tile_h must be a power of two in [32, 256], tile_w a power of two");
   if (opts->block_size && opts->block_size != 64 && opts->block_size != 128 &&
-      opts->block_size != 256)
-    return bh_fail(BH_E_INVALID, "bh_render_noalloc: block_size must be 64, 128 or 256");
+      opts->block_size != 256 && opts->block_size != 512)
+    return bh_fail(BH_E_INVALID, "bh_render_noalloc: block_size must be 64, 128, 256 or 512");
+  if (opts->queue_chunk && (opts->queue_chunk < 32 || opts->queue_chunk > 1024 || opts->queue_chunk % 32))
+    return bh_fail(BH_E_INVALID, "bh_render_noalloc: queue_chunk must be a multiple of 32 in [32, 1024]");
   if (opts->rtol < 0 || opts->atol < 0 || opts->phi_max < 0 || opts->h_max < 0 || opts->h_max_far < 0 || opts->rtol_far < 0 ||
-      opts->max_steps < 0 || opts->blocks_per_sm < 0)
+      opts->rtol_near < 0 || opts->band < 0 || opts->max_steps < 0 || opts->blocks_per_sm < 0)
     return bh_fail(BH_E_INVALID, "bh_render_noalloc: negative option");
   SceneK sk;
   int rc = noalloc_scene(desc, &sk);
@@ -140,6 +162,9 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     const bh_camera& b = cams[i];
     if (!(b.r_obs > 2.0 * sk.M) || !(b.tan_half > 0.0) || !std::isfinite(b.tan_half))
       return bh_fail(BH_E_INVALID, "bh_render_noalloc: camera %d not set or inside r = 2M", i);
+    if (!camera_looks_at_hole(b))
+      return bh_fail(BH_E_INVALID,
+                     "bh_render_noalloc: camera %d must look at the hole with an orthonormal basis", i);
     CamK& c = hc[i];
     for (int k = 0; k < 3; ++k) {
       c.pos[k] = b.pos[k];
@@ -156,12 +181,12 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
     c.tiles_y = (h[i] + th - 1) / th;
     c.q_off = q;
     c.out_off = o;
-    fill_cam_r(c, &c.f);
-    fill_cam_r(c, &c.d);
+    fill_cam_r(c, sk, &c.f);
+    fill_cam_r(c, sk, &c.d);
     fill_cam_peri(c, sk.f.M);
     fill_cam_band(c, sk.M, sk.ic, 0.0);  // no band pass here
     c.row_off = 0;
-    q += 32LL * c.tiles_x * c.tiles_y;
+    q += (long long)tw * th * c.tiles_x * c.tiles_y;
     o += (long long)w[i] * h[i];
   }
   if (q >= 0x7FFFFFFFLL || o >= 0x7FFFFFFFLL)
@@ -179,8 +204,14 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   cudaStream_t stream = (cudaStream_t)opts->stream;
   // the scratch keeps the previous call's contents: clear the counters
   e = cudaMemsetAsync(ws, 0, sizeof(WorkK), stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dcams, hc, n_cams * sizeof(CamK), cudaMemcpyHostToDevice, stream);
+  for (int i0 = 0; i0 < n_cams && e == cudaSuccess; i0 += kCamsPerCopy) {
+    CamChunk chunk;
+    memset(&chunk, 0, sizeof chunk);
+    chunk.n = std::min(kCamsPerCopy, n_cams - i0);
+    for (int i = 0; i < chunk.n; ++i) chunk.c[i] = hc[i0 + i];
+    k_noalloc_cams<<<1, 32, 0, stream>>>(chunk, dcams + i0);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return bh_cuda_fail(e, "bh_render_noalloc: upload");
 
   Params p;
@@ -190,21 +221,25 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   p.n_cams = n_cams;
   p.tile_w = tw;
   p.tile_h = th;
+  p.tile_shift = ilog2(tw * th);
+  p.tile_wshift = ilog2(tw);
+  p.chunk = opts->queue_chunk ? opts->queue_chunk : 32;
   p.n_queue = q;
   p.n_rays = o;
   p.rtol = opts->rtol > 0 ? opts->rtol : (f64 ? 1e-10 : 1e-5);
   p.atol = opts->atol > 0 ? opts->atol : (f64 ? 1e-10 : 1e-7);
   p.rtol64 = 1e-10;
   p.atol64 = 1e-10;
-  p.band = 0.0;
+  p.band = opts->band > 0 ? opts->band : 0.05;  // FP32: the rtol_near rays
   p.phi_max = opts->phi_max > 0 ? opts->phi_max : 64.0;
   p.h_max = opts->h_max > 0 ? opts->h_max : (f64 ? INFINITY : 0.3);
   p.h_max_far = opts->h_max_far > 0 ? opts->h_max_far : (f64 ? p.h_max : 0.5);
   p.rtol_far = opts->rtol_far > 0 ? opts->rtol_far : (f64 ? p.rtol : 10.0 * p.rtol);
+  p.rtol_near = opts->rtol_near > 0 ? opts->rtol_near : (f64 ? p.rtol : 0.01 * p.rtol);
   p.max_steps = opts->max_steps > 0 ? opts->max_steps : 100000;
   p.budget = p.max_steps;  // every ray finishes in the coherent pass
   p.peri_reset = 0;
-  p.abort_after = opts->abort_after;
+  p.abort_after = 0;
   p.dirs = out_dirs;
   p.flags = out_flags;
   p.rgba = out_rgba8;

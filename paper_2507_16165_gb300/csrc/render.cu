@@ -1,8 +1,9 @@
 // Persistent render kernels.
 //
-// The image is cut into 32-ray tiles (tile_w x tile_h pixels, camera-major),
-// one tile per warp grab from a global atomic queue.  A warp integrates its 32
-// neighbouring rays in lock step (coherent pass); a ray that needs more than
+// The image is cut into tiles of tile_w x tile_h pixels (32 to 256, camera-
+// major, row-major inside a tile); a warp grabs `chunk` queue slots at a time
+// from a global atomic counter and takes them 32 at a time.  It integrates
+// its 32 neighbouring rays in lock step (coherent pass); a ray that needs more than
 // `budget` attempted steps -- near the photon sphere the step count grows
 // like -ln|b - 3 sqrt(3) M| -- is saved to the long-ray list and finished by
 // a second persistent kernel whose lanes refill one ray at a time, so one
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool slot_pixel(const Params& p, long long q, int* ca
   }
   const CamK& c = p.cams[lo];
   const long long l = q - c.q_off;
-  const int tile = (int)(l >> 5), i = (int)(l & 31);
+  const int tile = (int)(l >> p.tile_shift), i = (int)(l & ((1 << p.tile_shift) - 1));
   // tile row from an FP32 estimate, corrected to the exact quotient (the
   // estimate is off by a few at most, for tile counts beyond 2^24)
   int ty = (int)((float)tile * c.f.inv_tiles_x);
@@ -81,9 +82,9 @@ __device__ __forceinline__ bool slot_pixel(const Params& p, long long q, int* ca
     ++ty;
     tx -= c.tiles_x;
   }
-  // tile_w * tile_h = 32, so tile_w is a power of two
+  // tile_w and the tile's slot count are powers of two
   const int x = tx * p.tile_w + (i & (p.tile_w - 1));
-  const int y = ty * p.tile_h + (i >> (__ffs(p.tile_w) - 1));
+  const int y = ty * p.tile_h + (i >> p.tile_wshift);
   *cam = lo;
   *px = x;
   *py = y;
@@ -171,8 +172,10 @@ __device__ __forceinline__ float acos_guess(float x) {
   return x >= 0.0f ? r : 3.14159265f - r;
 }
 
-__device__ __forceinline__ float periastron64(float M, double m2, float v0f, double k0, float k0f) {
-  const float E = fmaf(v0f, v0f, k0f);
+// Middle root of 2M u^3 - u^2 + E0 from E0 given in FP64 (and its FP32
+// rounding E): the FP32 start and Newton step, then the Newton step whose
+// residual is FP64.
+__device__ __forceinline__ float periastron_of_e(float M, double m2, float E, double E0) {
   if (!(M > 0.0f)) return sqrtf(E);
   const float x = fmaf(-54.0f * M * M, E, 1.0f);
   if (!(x > -1.0f)) return NAN;
@@ -180,11 +183,29 @@ __device__ __forceinline__ float periastron64(float M, double m2, float v0f, dou
   float u = fmaf(0.33333334f * im, __cosf(acos_guess(x) * 0.33333334f - 2.0943951f), 0.16666667f * im);
   const float m2f = 2.0f * M;
   u -= fmaf(u * u, fmaf(m2f, u, -1.0f), E) / (u * fmaf(3.0f * m2f, u, -2.0f));
-  const double vd = v0f;
-  const double E0 = fma(vd, vd, k0);
   const double ud = u;
   const double f = fma(ud * ud, fma(m2, ud, -1.0), E0);
   return fmaf(-(float)f, 1.0f / (u * fmaf(3.0f * m2f, u, -2.0f)), u);
+}
+
+__device__ __forceinline__ float periastron64(float M, double m2, float v0f, double k0, float k0f) {
+  const double vd = v0f;
+  return periastron_of_e(M, m2, fmaf(v0f, v0f, k0f), fma(vd, vd, k0));
+}
+
+// The same periastron for the ray through image point (px + ox, py + oy) of
+// camera c with 1/b^2 itself in FP64: rho^2 = sx^2 + sy^2 from the camera's
+// FP64 constants, 1/rho^2 from the FP32 reciprocal and one FP64 Newton step
+// (relative error about 1e-14), 1/b^2 = peri_A + peri_B / rho^2 (fill_cam_band).
+// Eleven operations on the FP64 pipe.
+__device__ __forceinline__ float periastron_b64(float M, const CamK& c, double px, double py) {
+  const double sx = fma(px, c.d.px_scale, -c.d.sx);
+  const double sy = fma(-py, c.d.py_scale, c.d.sy);
+  const double rho2 = fma(sx, sx, sy * sy);
+  const double y0 = (double)rcp_approx((float)rho2);
+  const double y = fma(y0, fma(-rho2, y0, 1.0), y0);
+  const double E0 = fma(c.peri_B, y, c.peri_A);
+  return periastron_of_e(M, 2.0 * (double)M, (float)E0, E0);
 }
 
 // Photon-sphere band of the MIXED mode as a test on the pixel: a camera
@@ -192,8 +213,11 @@ __device__ __forceinline__ float periastron64(float M, double m2, float v0f, dou
 // angle alpha with tan(alpha) = rho = |(sx, sy)| with the direction of the
 // hole, and its impact parameter grows with alpha.  The band
 // |b - 3 sqrt(3) M| < band is then rho^2 in (band_rho2_lo, band_rho2_hi),
-// bounds the host derives per camera.  The list builder and the passes that
-// skip band rays evaluate this same function, so they agree on every pixel.
+// bounds the host derives per camera in FP64.  The list builder and the
+// passes that skip band rays evaluate this same function, so they agree on
+// every pixel.  The comparison is in FP32: the band's edge is a policy, not a
+// physical boundary, and a pixel within the FP32 rounding of rho^2 (about
+// 1e-7 relative) of it is integrated by either pass within the bar.
 __device__ __forceinline__ bool band_pixel(const CamK& c, int px, int py) {
   const float sx = fmaf((float)px + 0.5f, c.f.px_scale, -c.f.sx);
   const float sy = fmaf(-((float)py + 0.5f), c.f.py_scale, c.f.sy);
@@ -205,27 +229,37 @@ __device__ __forceinline__ bool band_pixel(const CamK& c, int px, int py) {
 __device__ __forceinline__ long long pixel_slot(const Params& p, const CamK& c, int px, int py) {
   const int tx = px / p.tile_w, ty = py / p.tile_h;
   const int i = (py - ty * p.tile_h) * p.tile_w + (px - tx * p.tile_w);
-  return c.q_off + ((long long)ty * c.tiles_x + tx) * 32 + i;
+  return c.q_off + (((long long)ty * c.tiles_x + tx) << p.tile_shift) + i;
 }
 
 // Set up the ray of queue slot q.  Returns true when the ray is to be
 // integrated by the caller; false when it was padding, finished directly
 // (radial) or deferred to the FP64 band list.
-template <typename R, int MODE, typename OutR, bool SPP = false>
+// WCULL: the 32 lanes of the warp call it together for a group of 32 slots
+// (one camera) and share one sphere cull (warp_sphere_candidates); else each
+// ray tests every sphere.
+template <typename R, int MODE, typename OutR, bool SPP = false, bool WCULL = false>
 __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out,
                            R ox = R(0.5), R oy = R(0.5), SppAcc* acc = nullptr) {
   int cam, px, py, out;
-  if (!slot_pixel(p, q, &cam, &px, &py, &out)) return false;
+  const bool in_image = slot_pixel(p, q, &cam, &px, &py, &out);
   const CamK& c = p.cams[cam];
+  const CamR<R>& C = CR<R>(c);
+  // image-plane point of the ray (pixel centre, or a sub-pixel sample)
+  const R sx = m_fma(R(px) + ox, C.px_scale, -C.sx);
+  const R sy = m_fma(-(R(py) + oy), C.py_scale, C.sy);
+  unsigned cand = (1u << p.s.n_sph) - 1u;
+  if (WCULL) cand = warp_sphere_candidates<R>(p.s, c, sx, sy);
+  if (q >= p.n_queue || !in_image) return false;
   // band rays belong to the FP64 pass (listed by k_band_list)
   if (MODE == MODE_MIXED && band_pixel(c, px, py)) return false;
-  R P[3], d[3];
-  camera_ray<R>(c, px, py, P, d, ox, oy);
   r.out = out;
   r.aux = (MODE == MODE_FP64 || MODE == MODE_BAND64) ? BH_FLAG_FP64 : 0u;
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
-  if (plane_setup<R>(p.s, P, d, CR<R>(c).r_obs, CR<R>(c).ir, r, &b, &cos_a)) {
+  if (plane_setup<R>(p.s, c, sx, sy, cand, r, &b, &cos_a)) {
+    R P[3], d[3];
+    camera_ray<R>(c, px, py, P, d, ox, oy);
     st.count_flag(radial_ray<R, OutR, SPP>(p, P, d, cos_a, out, r.aux, acc));
     return false;
   }
@@ -234,11 +268,16 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
   // rays at least kFarB from the critical impact parameter, whose exit
   // directions amplify stepping errors far less
-  const bool far = !d64 && m_abs(b - SR<R>(p.s).b_crit) >= R(kFarB) * SR<R>(p.s).M;
+  const R db = m_abs(b - SR<R>(p.s).b_crit);
+  const bool far = !d64 && db >= R(kFarB) * SR<R>(p.s).M;
   if (MODE == MODE_MIXED) {
     // the FP64 turning point of near-critical rays (all rays with
     // peri_reset == 2); the others step through it in FP32
-    if ((p.peri_reset == 2 || (p.peri_reset == 1 && !far)) && r.v > R(0)) {
+    if (p.peri_reset == 2 && r.v > R(0)) {
+      // every ray with a turning point, 1/b^2 from the FP64 image radius
+      r.up = R(periastron_b64(p.s.f.M, c, (double)px + (double)ox, (double)py + (double)oy));
+      r.tp = R(0);
+    } else if (p.peri_reset == 1 && !far && r.v > R(0)) {
       r.up = R(periastron64(p.s.f.M, 2.0 * (double)p.s.f.M, float(r.v), c.peri_k0, c.peri_k0f));
       r.tp = R(0);
     } else {
@@ -254,6 +293,13 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01)) : tol.h_max;
   // far FP32 rays may take longer steps; they still start at h_max
   if (far) r.aux |= kAuxFar;
+  // the FP32 form's near-critical rays, which the other forms integrate in
+  // FP64, are held to rtol_near
+  if (MODE == MODE_FP32 && db < tol.band) r.aux |= kAuxNear;
+  // the tier as two per-ray constants, so a step multiplies and clamps
+  // instead of testing the tier bits
+  r.es = far ? tol.far_e2 : ((MODE == MODE_FP32 && db < tol.band) ? tol.near_e2 : R(1));
+  r.hc = far ? tol.h_far : tol.h_max;
   return true;
 }
 
@@ -447,15 +493,16 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
   R un, vn, fn, err2;
   dp5_attempt<R>(S.M3, r.u, r.v, r.f, r.h, tol.rtol, tol.atol, un, vn, fn, err2);
-  // rays far from the critical impact parameter (FP32 passes only) are held
-  // to rtol_far, atol scaled alike: their error norm scales by rtol/rtol_far
-  if (r.aux & kAuxFar) err2 *= tol.far_e2;
+  // rays far from the critical impact parameter (FP32 passes) are held to
+  // rtol_far, the FP32 form's near-critical rays to rtol_near, atol scaled
+  // alike: their squared error norm scales by (rtol / rtol_tier)^2
+  err2 *= r.es;
   r.steps++;
   st.c[ST_STEPS]++;
   if (sizeof(R) == 8) st.c[ST_STEPS64]++;
   const R h = r.h;
   r.h = h * step_factor<R>(err2);
-  r.h = m_min(r.h, (r.aux & kAuxFar) ? tol.h_far : tol.h_max);
+  r.h = m_min(r.h, r.hc);
   if (!(err2 <= R(1))) {
     st.c[ST_REJ]++;
     if (r.steps >= p.max_steps) {
@@ -500,7 +547,32 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   return false;
 }
 
-// Coherent pass: one 32-ray tile per warp grab, lanes in lock step, rays
+// Persistent work loop of a warp: each grab of the global counter takes
+// p.chunk queue slots, handed to body() 32 at a time (lane i gets slot
+// g + i of each 32-slot group g); the loop ends with the queue or at the
+// host's abort slot.  Queue windows and lengths are multiples of 32.
+template <typename F>
+__device__ __forceinline__ void for_each_grab(const Params& p, LocalStats& st, F&& body) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0)
+      base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, (unsigned long long)p.chunk);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned long long)p.n_queue) break;
+    if (p.abort_after && base >= p.abort_after) {
+      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
+      break;
+    }
+    if (lane == 0) st.c[ST_GRABS]++;
+    const unsigned long long end =
+        base + (unsigned long long)p.chunk < (unsigned long long)p.n_queue
+            ? base + (unsigned long long)p.chunk : (unsigned long long)p.n_queue;
+    for (unsigned long long g = base; g < end; g += 32) body((long long)g + lane);
+  }
+}
+
+// Coherent pass: 32 rays of a grab at a time, lanes in lock step, rays
 // over the step budget moved to the long-ray list.
 // The lanes of a warp integrate their rays in lock step until each has
 // ended (finished and stored) or used its step budget (moved to the
@@ -534,10 +606,11 @@ __device__ __forceinline__ void integrate_warp(const Params& p, Ray<R>& r, bool 
   }
 }
 
-// Resident 256-thread blocks per SM the register allocation must allow:
-// 4 (64 registers) for FP32, 2 for FP64.  At 64 registers the FP32 kernels
-// spill a few words but run 2% faster than at 80 with three blocks.
-template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 4 : 2;
+// Resident 512-thread blocks per SM the register allocation must allow:
+// 2 (64 registers) for FP32, 1 (128 registers) for FP64; blocks of up to 512
+// threads may be launched.  At 64 registers the FP32 kernels spill a few
+// words but run 2% faster than at 80 with three 256-thread blocks.
+template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 
 // Re-create a ray from its queue slot and, for a long ray, its saved state.
 template <typename R, int MODE, typename OutR>
@@ -627,13 +700,45 @@ __device__ __forceinline__ void list_pass(const Params& p, LocalStats& st) {
 // The FP64 band pass is held to 64 registers, so one band warp and seven
 // 128-thread FP32 blocks fill an SM sub-partition's register file; it lets
 // the dependent coherent pass launch at once (see k_coherent).
+// The long-ray pass over spilled rays is launched as the programmatic
+// dependent of the pass that spills them, so its blocks are scheduled while
+// that pass drains; it waits for the pass to complete (and its spill list
+// to be visible) before reading the list.
 template <typename R, int MODE, typename OutR, int SRC>
-__global__ void __launch_bounds__(256, MODE == MODE_BAND64 ? 4 : kMinBlocks<R>)
+__global__ void __launch_bounds__(512, MODE == MODE_BAND64 ? 2 : kMinBlocks<R>)
     k_longrays(const __grid_constant__ Params p) {
   if (SRC == SRC_BAND) pdl_launch_dependents();
+  if (SRC == SRC_SPILL) pdl_wait_primary();
   LocalStats st;
   st.zero();
   list_pass<R, MODE, OutR, SRC>(p, st);
+  st.flush(p.ws);
+}
+
+// Lock-step pass over the surrogate's fallback list: a warp takes 32
+// consecutive list entries at a time -- rays a surrogate warp listed
+// together, neighbours in the image -- and integrates them as the coherent
+// pass does, rays over the step budget moving to the long-ray list.
+template <typename R, int MODE, typename OutR>
+__global__ void __launch_bounds__(512, kMinBlocks<R>) k_listwarp(const __grid_constant__ Params p) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = *(volatile unsigned long long*)&p.ws->surr_count;
+  LocalStats st;
+  st.zero();
+  for (long long guard = 0; guard < (1ll << 40); ++guard) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ws->surr_next, 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= total) break;
+    if (lane == 0) st.c[ST_GRABS]++;
+    const unsigned long long idx = base + lane;
+    const long long q = idx < total ? (long long)p.surr_list[idx] : -1;
+    Ray<R> r;
+    SphWin win;
+    r.win = &win;
+    const bool active = q >= 0 && restore_ray<R, MODE, OutR>(p, q, nullptr, r, st);
+    integrate_warp<R, MODE, OutR>(p, r, active, q, st);
+  }
   st.flush(p.ws);
 }
 
@@ -642,27 +747,18 @@ __global__ void __launch_bounds__(256, MODE == MODE_BAND64 ? 4 : kMinBlocks<R>)
 // (and take the band warps' places as they leave); each block waits for the
 // band pass to complete before it exits, so the render ends after both.
 template <typename R, int MODE, typename OutR, bool SPP = false>
-__global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(512, kMinBlocks<R>) k_coherent(const __grid_constant__ Params p) {
+  // the long-ray pass may be scheduled now; it waits for this grid to end
+  pdl_launch_dependents();
   LocalStats st;
   st.zero();
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
-    base = __shfl_sync(kFull, base, 0);
-    if (base >= (unsigned long long)p.n_queue) break;
-    if (p.abort_after && base >= p.abort_after) {
-      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
-      break;
-    }
-    if (lane == 0) st.c[ST_GRABS]++;
-    const long long q = (long long)base + lane;
+  for_each_grab(p, st, [&](long long q) {
     if (!SPP) {
       Ray<R> r;
       SphWin win;
       r.win = &win;
       R b;
-      bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
+      bool active = setup_slot<R, MODE, OutR, false, true>(p, q, r, st, &b);
       integrate_warp<R, MODE, OutR>(p, r, active, q, st);
     } else {
       // n x n stratified samples per pixel, then the ray through the centre
@@ -682,8 +778,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
         r.win = &win;
         R b;
         r.out = -1;
-        bool active =
-            (q < p.n_queue) && setup_slot<R, MODE, OutR, true>(p, q, r, st, &b, ox, oy, &acc);
+        bool active = setup_slot<R, MODE, OutR, true, true>(p, q, r, st, &b, ox, oy, &acc);
         if (r.out >= 0) out = r.out;
         integrate_warp<R, MODE, OutR, true>(p, r, active, q, st, &acc);
       }
@@ -692,7 +787,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
         p.rgba[out] = pack_rgba(acc.c[0] * w, acc.c[1] * w, acc.c[2] * w);
       }
     }
-  }
+  });
   st.flush(p.ws);
   if (MODE == MODE_MIXED) pdl_wait_primary();
 }
@@ -706,10 +801,15 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_coherent(const __grid_co
 // threshold -- run the MLP for the whole warp on the tensor cores and shade
 // the rays it answers: a served ray escapes at phi_inf = alpha + delta
 // unless the disk is met at psi0 or psi0 + pi first (u b from the MLP gives
-// the crossing radius).  The warp then integrates the rest in lock step with
-// the FP32 integrator, as the coherent pass would.
-// 128-thread blocks, three per SM: room stays for the FP64 band pass.
-__global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Params p) {
+// the crossing radius).  The rays it does not answer go to a list that the
+// FP32 integrator's list pass finishes after this pass: with the integrator
+// inline, the pass's code outgrew the instruction cache and its warps waited
+// on instruction fetch for most of their cycles.
+// 128-thread blocks, three per SM, at most 144 registers a thread: the
+// three blocks (55,296 registers) and the FP64 band pass's four 64-register
+// warps (8,192) fit in an SM's 65,536 together, so the band pass runs beside
+// this pass instead of after it.
+__global__ void __maxnreg__(144) k_surrogate(const __grid_constant__ Params p) {
   __shared__ uint2 s_frag[bhs::NFRAG];
   __shared__ float s_bias[bhs::NBIAS];
   __shared__ float s_feat[4][32 * bhs::K0];  // feature rows of each warp
@@ -723,22 +823,12 @@ __global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Pa
   const float bc_m = 5.19615242270663188f;  // 3 sqrt 3: b_crit / M
   LocalStats st;
   st.zero();
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
-    base = __shfl_sync(kFull, base, 0);
-    if (base >= (unsigned long long)p.n_queue) break;
-    if (p.abort_after && base >= p.abort_after) {
-      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
-      break;
-    }
-    if (lane == 0) st.c[ST_GRABS]++;
-    const long long q = (long long)base + lane;
+  for_each_grab(p, st, [&](long long q) {
     Ray<float> r;
     SphWin win;
     r.win = &win;
     float b = 0.0f;
-    bool active = (q < p.n_queue) && setup_slot<float, MODE_MIXED, float>(p, q, r, st, &b);
+    bool active = setup_slot<float, MODE_MIXED, float, false, true>(p, q, r, st, &b);
     bool serve = false;
     float r_obs = 0.0f;
     float f[bhs::K0];
@@ -757,6 +847,7 @@ __global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Pa
       serve = ok;
     }
     if (__any_sync(kFull, serve)) {
+      if (lane == 0) st.c[ST_MLP] += 32;
       for (int k = 0; k < bhs::K0; ++k) feat[lane * bhs::K0 + k] = f[k];
       __syncwarp();
       float o[3];
@@ -796,9 +887,18 @@ __global__ void __launch_bounds__(128, 3) k_surrogate(const __grid_constant__ Pa
         }
       }
     }
-    if (active) st.c[ST_FALLBACK]++;
-    integrate_warp<float, MODE_MIXED, float>(p, r, active, q, st);
-  }
+    // the rest go to the integrator's list: one atomic per warp
+    const unsigned fb = __ballot_sync(kFull, active);
+    if (fb) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&p.ws->surr_count, (unsigned long long)__popc(fb));
+      base = __shfl_sync(kFull, base, 0);
+      if (active) {
+        p.surr_list[base + __popc(fb & ((1u << lane) - 1u))] = (int)q;
+        st.c[ST_FALLBACK]++;
+      }
+    }
+  });
   st.flush(p.ws);
 }
 
@@ -899,7 +999,9 @@ __device__ __forceinline__ bool paper_step(const Params& p, Ray<R>& r, R eps, R 
   r.steps++;
   st.c[ST_STEPS]++;
   if (sizeof(R) == 8) st.c[ST_STEPS64]++;
-  const R pa = r.phi, pb = pa + eps;
+  // the points lie at phi = k eps: formed from the step count, since a sum
+  // of hundreds of FP32 additions of eps drifts by 1e-4 rad
+  const R pa = r.phi, pb = R(r.steps) * eps;
   if (un <= R(0)) {
     hit.flags = BH_FLAG_ESC;
     hit.phi = m_fma(eps, m_div(r.u, r.u - un), pa);
@@ -966,29 +1068,18 @@ __device__ __forceinline__ bool paper_step(const Params& p, Ray<R>& r, R eps, R 
 }
 
 template <typename R, typename OutR>
-__global__ void __launch_bounds__(256, kMinBlocks<R>) k_paper(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(512, kMinBlocks<R>) k_paper(const __grid_constant__ Params p) {
   constexpr int MODE = sizeof(R) == 8 ? MODE_FP64 : MODE_FP32;
-  const int lane = threadIdx.x & 31;
   const R eps = R(p.paper_eps);
   const R u_capt = SR<R>(p.s).M > R(0) ? R(0.5) / SR<R>(p.s).M : R(INFINITY);
   LocalStats st;
   st.zero();
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, 32ull);
-    base = __shfl_sync(kFull, base, 0);
-    if (base >= (unsigned long long)p.n_queue) break;
-    if (p.abort_after && base >= p.abort_after) {
-      if (lane == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
-      break;
-    }
-    if (lane == 0) st.c[ST_GRABS]++;
-    const long long q = (long long)base + lane;
+  for_each_grab(p, st, [&](long long q) {
     Ray<R> r;
     SphWin win;
     r.win = &win;
     R b;
-    bool active = (q < p.n_queue) && setup_slot<R, MODE, OutR>(p, q, r, st, &b);
+    bool active = setup_slot<R, MODE, OutR, false, true>(p, q, r, st, &b);
     if (active) r.steps = 0;
     while (__any_sync(kFull, active)) {
       if (active) {
@@ -1000,7 +1091,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_paper(const __grid_const
         }
       }
     }
-  }
+  });
   st.flush(p.ws);
 }
 
@@ -1025,6 +1116,24 @@ static int occupancy(K kernel, int block) {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0);
   return n > 0 ? n : 1;
+}
+
+// Launch `kernel` as the programmatic dependent of the previous kernel on
+// `stream` (it must call pdl_wait_primary before reading that kernel's
+// results).
+template <typename K>
+static void launch_dependent(K kernel, int grid, int block, cudaStream_t stream, const Params& p) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)grid);
+  lc.blockDim = dim3((unsigned)block);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, kernel, p);
 }
 
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
@@ -1077,17 +1186,17 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
   } else if (mode == MODE_FP64) {
     auto k1 = k_coherent<double, MODE_FP64, double>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
-    rec(1);
     auto k2 = k_longrays<double, MODE_FP64, double, SRC_SPILL>;
-    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    launch_dependent(k2, grid_of(k2), block, stream, p);
+    rec(1);
     rec(2);
     rec(3);
   } else if (mode == MODE_FP32) {
     auto k1 = k_coherent<float, MODE_FP32, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
-    rec(1);
     auto k2 = k_longrays<float, MODE_FP32, float, SRC_SPILL>;
-    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    launch_dependent(k2, grid_of(k2), block, stream, p);
+    rec(1);
     rec(2);
     rec(3);
   } else if (ls.mixed_part == 1) {
@@ -1103,9 +1212,9 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     // and the long rays
     auto k1 = k_coherent<float, MODE_MIXED, float>;
     k1<<<grid_of(k1), block, 0, stream>>>(p);
-    rec(1);
     auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
-    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    launch_dependent(k2, grid_of(k2), block, stream, p);
+    rec(1);
     rec(2);
     rec(3);
   } else {
@@ -1127,9 +1236,9 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
     lc.attrs = attr;
     lc.numAttrs = 1;
     cudaLaunchKernelEx(&lc, k1, p);
-    rec(1);
     auto k2 = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
-    k2<<<grid_of(k2), block, 0, stream>>>(p);
+    launch_dependent(k2, grid_of(k2), block, stream, p);
+    rec(1);
     rec(2);
     rec(3);
   }
@@ -1159,9 +1268,14 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
   if (ls.band_ev) record(ls.band_ev[1], ls.side);
   cudaEventRecord(ls.join, ls.side);
   k_surrogate<<<ls.num_sms * 3, 128, 0, stream>>>(p);
+  // the integrator finishes the rays the network did not answer; it follows
+  // in stream order (as a programmatic dependent its waiting blocks would
+  // take the SM room the FP64 band pass runs in)
   if (ev) record(ev[1], stream);
+  auto kw = k_listwarp<float, MODE_MIXED, float>;
+  kw<<<ls.num_sms * occupancy(kw, ls.block), ls.block, 0, stream>>>(p);
   auto kl = k_longrays<float, MODE_MIXED, float, SRC_SPILL>;
-  kl<<<ls.num_sms * occupancy(kl, ls.block), ls.block, 0, stream>>>(p);
+  launch_dependent(kl, ls.num_sms * occupancy(kl, ls.block), ls.block, stream, p);
   if (ev) record(ev[2], stream);
   cudaStreamWaitEvent(stream, ls.join, 0);
   if (ev) record(ev[3], stream);

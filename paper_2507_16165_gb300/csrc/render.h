@@ -31,9 +31,10 @@ cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cuda
                           cudaEvent_t* ev);
 
 // Launch a surrogate render: band pre-pass, FP64 band pass on the side
-// stream, the surrogate pass (which integrates the rays it does not answer
-// itself), then the long-ray pass.  ev[0..3]: start, after the surrogate
-// pass, after the long-ray pass, end.
+// stream, the surrogate pass (which lists the rays it does not answer), the
+// integrator's lock-step pass over that list and the long-ray pass.
+// ev[0..3]: start, after the surrogate pass, after the integrator passes,
+// end.
 cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_t stream,
                              cudaEvent_t* ev);
 

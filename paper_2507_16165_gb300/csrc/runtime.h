@@ -50,11 +50,11 @@ struct bh_scene {
 // Resolved options of one render.
 struct RenderConfig {
   int mode;
-  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, rtol_far, paper_eps;
+  double rtol, atol, band, band_rtol, phi_max, h_max, h_max_far, rtol_far, rtol_near, paper_eps;
   int spp_n;  // samples per pixel side
   int doppler;
   int max_steps;
-  int block, blocks_per_sm, tile_w, tile_h, budget;
+  int block, blocks_per_sm, tile_w, tile_h, budget, chunk;
   int band_lanes, band_warps;
   int peri_reset;
   unsigned long long abort_after;
@@ -63,6 +63,7 @@ struct RenderConfig {
 // Launch shape picked by the autotuner (or the built-in default).
 struct TunedShape {
   int block, blocks_per_sm, tile_w, tile_h, budget;
+  int chunk;  // queue slots per warp grab
   int band_lanes, band_warps;  // MIXED FP64 band pass: lanes per warp, warps per SM
 };
 
@@ -76,6 +77,10 @@ class DeviceGuard {
 };
 
 int bh_fail(int code, const char* fmt, ...);
+// A camera the kernels can render: it looks at the hole (fwd = -pos / r_obs)
+// with right and up an orthonormal image basis perpendicular to fwd, as
+// bh_camera_set makes it.
+bool camera_looks_at_hole(const bh_camera& c);
 int bh_cuda_fail(cudaError_t e, const char* what);
 int check_render_args(const bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
                       const int* h, const bh_render_opts* opts);
@@ -106,7 +111,10 @@ int render_device(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w,
 TunedShape tuned_shape(const bh_scene* sc, int mode);
 
 // surrogate.cu
+int surrogate_prepare(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                      void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
+                      cudaStream_t upload_stream, bhk::CamK* cams_dev, PreparedRender* pr);
+int surrogate_enqueue(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream);
 int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
-                     void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
-                     const RenderConfig& cfg);
+                     void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts);
 void surrogate_release(bh_scene* sc);

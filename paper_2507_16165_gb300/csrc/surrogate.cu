@@ -915,22 +915,30 @@ extern "C" int bh_surrogate_load(bh_scene* sc, const char* path) {
 // ---------------------------------------------------------------------------
 // Surrogate render
 // ---------------------------------------------------------------------------
-int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
-                     void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
-                     const RenderConfig& cfg) {
+// Host-side preparation of a surrogate render: the integrator passes run in
+// MIXED arithmetic with the launch shape tuned for the surrogate mode; the
+// fallback list is sized; the FP64 band pass is set to run on the scene's
+// side stream.  cams_dev as for prepare_render.
+int surrogate_prepare(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                      void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
+                      cudaStream_t upload_stream, CamK* cams_dev, PreparedRender* pr) {
   if (!sc->surr || !sc->surr->d_frag)
     return bh_fail(BH_E_NO_SURROGATE, "surrogate mode: no trained weights on this scene");
   if (sc->sk.ic != BH_IC_STATIC && sc->sk.ic != BH_IC_EUCLIDEAN)
     return bh_fail(BH_E_INVALID, "surrogate mode: unknown initial-condition convention");
-  cudaStream_t stream = (cudaStream_t)opts->stream;
-  // the integrator passes run in MIXED arithmetic
+  const TunedShape t = tuned_shape(sc, BH_MODE_SURROGATE);
   bh_render_opts o = *opts;
   o.mode = BH_MODE_MIXED;
-  PreparedRender pr;
-  int rc = prepare_render(sc, cams, n_cams, w, h, dirs, flags, rgba, &o, stream, nullptr, &pr);
+  if (!o.tile_w && !o.tile_h) {
+    o.tile_w = t.tile_w;
+    o.tile_h = t.tile_h;
+  }
+  if (!o.queue_chunk) o.queue_chunk = t.chunk;
+  if (!o.budget) o.budget = t.budget;
+  int rc = prepare_render(sc, cams, n_cams, w, h, dirs, flags, rgba, &o, upload_stream, cams_dev, pr);
   if (rc) return rc;
   SurrogateState* s = sc->surr;
-  const size_t need = (size_t)pr.p.n_queue;
+  const size_t need = (size_t)pr->p.n_queue;
   if (s->list_cap < need) {
     if (s->d_list) cudaFree(s->d_list);
     s->d_list = nullptr;
@@ -940,20 +948,37 @@ int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int*
     s->list_cap = need;
   }
   // the FP64 band pass runs on the side stream beside the surrogate pass
-  pr.ls.side = sc->side;
-  pr.ls.fork = sc->fork;
-  pr.ls.join = sc->join;
-  pr.ls.band_ev = sc->band_ev;
-  pr.ls.band_warps = cfg.band_warps;
-  pr.p.mlp_frag = s->d_frag;
-  pr.p.mlp_bias = s->d_bias;
-  pr.p.surr_table = s->d_table;
-  pr.p.surr_nb_lb = s->nb_lb;
-  pr.p.surr_nb_r = s->nb_r;
-  pr.p.surr_list = s->d_list;
+  pr->ls.side = sc->side;
+  pr->ls.fork = sc->fork;
+  pr->ls.join = sc->join;
+  pr->ls.band_ev = sc->band_ev;
+  pr->ls.band_warps = t.band_warps;
+  pr->p.mlp_frag = s->d_frag;
+  pr->p.mlp_bias = s->d_bias;
+  pr->p.surr_table = s->d_table;
+  pr->p.surr_nb_lb = s->nb_lb;
+  pr->p.surr_nb_r = s->nb_r;
+  pr->p.surr_list = s->d_list;
+  pr->mode = BH_MODE_SURROGATE;
+  return BH_OK;
+}
+
+// Device work of a prepared surrogate render (also what a graph captures).
+int surrogate_enqueue(bh_scene* sc, const PreparedRender& pr, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(sc->d_ws, 0, sizeof(WorkK), stream);
   if (e == cudaSuccess) e = launch_surrogate(pr.p, pr.ls, stream, sc->ev);
   if (e != cudaSuccess) return bh_cuda_fail(e, "surrogate render: launch");
+  return BH_OK;
+}
+
+int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
+                     void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts) {
+  cudaStream_t stream = (cudaStream_t)opts->stream;
+  PreparedRender pr;
+  int rc = surrogate_prepare(sc, cams, n_cams, w, h, dirs, flags, rgba, opts, stream, nullptr, &pr);
+  if (rc) return rc;
+  rc = surrogate_enqueue(sc, pr, stream);
+  if (rc) return rc;
   sc->last_stream = stream;
   sc->timed = true;
   sc->band_used = true;

@@ -386,6 +386,9 @@ struct Ray {
   R phi_sph;             // next sphere-window start, or +inf
   R phi_evt;             // min(phi_node, phi_sph, phi_max): steps ending
                          // before it need no event search
+  R es;                  // scale of the squared error norm: the ray's tolerance
+                         // tier (1, (rtol/rtol_far)^2 or (rtol/rtol_near)^2)
+  R hc;                  // step-size cap of the ray's tier (h_max or h_max_far)
   R up;                  // periastron u of the orbit (MIXED reset), NaN if none
   R tp;                  // MIXED: 0 while the turning-point reset is pending, else -inf
   unsigned sph_mask;     // spheres whose in-plane circle is non-empty
@@ -397,6 +400,7 @@ struct Ray {
 
 constexpr unsigned kAuxPeriDone = 1u << 16;
 constexpr unsigned kAuxFar = 1u << 17;  // ray takes the relaxed step cap h_far
+constexpr unsigned kAuxNear = 1u << 18; // FP32 form: ray held to rtol_near
 
 // Event produced when a ray terminates.
 template <typename R>
@@ -427,13 +431,12 @@ __device__ __forceinline__ void camera_ray(const CamK& c, int px, int py, R P[3]
 
 // Angular window [phi_c - dphi, phi_c + dphi] of sphere k in the ray's
 // plane: the directions from the hole that meet the sphere's in-plane
-// circle.  Evaluated once per ray in single precision for both arithmetic
-// types (it only gates the exact test) and widened by 1e-4 rad.
+// circle.  (cx, cy): the sphere centre in the plane's basis.  Evaluated once
+// per ray in single precision for both arithmetic types (it only gates the
+// exact test) and widened by 1e-4 rad.
 template <typename R>
-__device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, int k) {
-  const float c0 = s.f.c[k][0], c1 = s.f.c[k][1], c2 = s.f.c[k][2];
-  const float cx = c0 * (float)r.e1x + c1 * (float)r.e1y + c2 * (float)r.e1z;
-  const float cy = c0 * (float)r.e2x + c1 * (float)r.e2y + c2 * (float)r.e2z;
+__device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, int k, float cx,
+                                                    float cy) {
   const float rho2 = cx * cx + cy * cy;
   const float rp2 = fmaxf(0.0f, s.f.rad[k] * s.f.rad[k] - (s.f.c2[k] - rho2));
   float pc = m_atan2(cy, cx);
@@ -465,44 +468,71 @@ __device__ __forceinline__ R next_sphere_window(const Ray<R>& r, R phi_from) {
   return R(best);
 }
 
-// Orbital-plane set-up of a camera ray.  Returns 0 for a ray to integrate,
-// 1 for a radial ray (handled by the caller with straight-line geometry).
+// Spheres whose circle the orbital plane of some ray of this warp's 32 rays
+// may cut (all lanes call it; the rays share one camera).  With the plane's
+// normal n = (sx up - sy right) / rho, sphere k is cut when
+// g(sx, sy) = |sx (up . c_k) - sy (right . c_k)| - R_k rho < 0.  g changes by
+// at most (|c_k| + R_k) per unit distance in the image plane, so when it is
+// positive by more than that times the distance from lane 0's point to the
+// farthest point of the group (plus a pixel diagonal, for sub-pixel samples)
+// no ray of the group cuts the sphere.  The exact test per ray follows for
+// the spheres that remain.
 template <typename R>
-__device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs, R ir, Ray<R>& r,
-                           R* b_out, R* cos_a_out, R* sin_a_out = nullptr) {
-  r.e1x = P[0] * ir;
-  r.e1y = P[1] * ir;
-  r.e1z = P[2] * ir;
-  R cr0 = P[1] * d[2] - P[2] * d[1];
-  R cr1 = P[2] * d[0] - P[0] * d[2];
-  R cr2 = P[0] * d[1] - P[1] * d[0];
-  const R sn2 = cr0 * cr0 + cr1 * cr1 + cr2 * cr2;
-  const R cos_a = d[0] * r.e1x + d[1] * r.e1y + d[2] * r.e1z;
-  *cos_a_out = cos_a;
-  const R rad = Num<R>::radial * r_obs;
-  if (sn2 < rad * rad) {
+__device__ __forceinline__ unsigned warp_sphere_candidates(const SceneK& s, const CamK& cam, R sx,
+                                                           R sy) {
+  const unsigned full = 0xFFFFFFFFu;
+  const float fx = (float)sx, fy = (float)sy;
+  const float x0 = __shfl_sync(full, fx, 0), y0 = __shfl_sync(full, fy, 0);
+  const float dx = fx - x0, dy = fy - y0;
+  const float d2 = fmaf(dx, dx, dy * dy);
+  const float dmax = sqrtf(__uint_as_float(__reduce_max_sync(full, __float_as_uint(d2))));
+  const float reach = fmaf(dmax + cam.f.pdiag, 1.0001f, 1e-5f);
+  const int k = threadIdx.x & 31;
+  bool maybe = false;
+  if (k < s.n_sph) {
+    const float rho0 = sqrtf(fmaf(x0, x0, y0 * y0));
+    const float g = fabsf(fmaf(x0, cam.f.uc[k], -y0 * cam.f.rc[k])) - s.f.rad[k] * rho0;
+    maybe = g <= (s.f.cnorm[k] + s.f.rad[k]) * reach;
+  }
+  return __ballot_sync(full, maybe);
+}
+
+// Orbital-plane set-up of the ray through image-plane point (sx, sy) of
+// camera cam.  Returns 0 for a ray to integrate, 1 for a radial ray (handled
+// by the caller with straight-line geometry).  cand: the spheres to test
+// for a cut of the plane (warp_sphere_candidates, or all of them).
+template <typename R>
+__device__ int plane_setup(const SceneK& s, const CamK& cam, R sx, R sy, unsigned cand, Ray<R>& r,
+                           R* b_out, R* cos_a_out) {
+  const CamR<R>& C = CR<R>(cam);
+  r.e1x = -C.fwd[0];
+  r.e1y = -C.fwd[1];
+  r.e1z = -C.fwd[2];
+  const R rho2 = m_fma(sx, sx, sy * sy);
+  // |P x d| / |P| = sin(alpha) = rho / sqrt(1 + rho^2); cos(alpha) = d . e1
+  const R iL = m_rsqrt(R(1) + rho2);
+  *cos_a_out = -iL;
+  if (rho2 < R(Num<R>::radial) * R(Num<R>::radial)) {
     *b_out = R(0);
     return 1;
   }
-  const R isn = m_rsqrt(sn2);
-  const R nx = cr0 * isn, ny = cr1 * isn, nz = cr2 * isn;
-  r.e2x = ny * r.e1z - nz * r.e1y;
-  r.e2y = nz * r.e1x - nx * r.e1z;
-  r.e2z = nx * r.e1y - ny * r.e1x;
-  const R sin_a = d[0] * r.e2x + d[1] * r.e2y + d[2] * r.e2z;
-  if (sin_a_out) *sin_a_out = sin_a;
+  const R irho = m_rsqrt(rho2);
+  r.e2x = m_fma(sx, C.right[0], sy * C.up[0]) * irho;
+  r.e2y = m_fma(sx, C.right[1], sy * C.up[1]) * irho;
+  r.e2z = m_fma(sx, C.right[2], sy * C.up[2]) * irho;
+  const R sin_a = rho2 * irho * iL;
   const SceneR<R>& S = SR<R>(s);
   const R M = S.M;
-  const R u0 = ir;
-  const R cot = m_div(cos_a, sin_a);
+  const R u0 = C.ir;
   R b;
   if (s.ic == 0) {
-    b = r_obs * sin_a * m_rsqrt(R(1) - R(2) * M * ir);
-    r.v = -u0 * cot * m_sqrt(R(1) - R(2) * M * u0);
+    b = C.kb * sin_a;
   } else {
-    b = r_obs * sin_a * m_rsqrt(R(1) - R(2) * M * sin_a * sin_a * ir);
-    r.v = -u0 * cot;
+    b = C.r_obs * sin_a * m_rsqrt(R(1) - R(2) * M * sin_a * sin_a * u0);
   }
+  // u'0 = -u0 cot(alpha) sqrt(1 - 2M u0) (static) or -u0 cot(alpha), with
+  // cot(alpha) = -1 / rho
+  r.v = C.kv * irho;
   *b_out = b;
   r.u = u0;
   r.f = accel(S.M3, u0);
@@ -518,27 +548,22 @@ __device__ int plane_setup(const SceneK& s, const R P[3], const R d[3], R r_obs,
       r.phi_node = (p0 > R(0)) ? p0 : Num<R>::pi;
     }
   }
-  // spheres cut by the plane and not wholly inside the orbit's periastron
-  // (SceneR::cull_b)
+  // spheres cut by the plane (|n . c_k| < R_k) and not wholly inside the
+  // orbit's periastron (SceneR::cull_b); their windows from the centre's
+  // coordinates in the plane, c . e1 (per camera) and c . e2
   unsigned mask = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxSph; ++k) {
-    if (k < s.n_sph) {
-      const R sd = nx * S.c[k][0] + ny * S.c[k][1] + nz * S.c[k][2];
-      if (m_abs(sd) < S.rad[k] && b <= S.cull_b[k]) mask |= 1u << k;
+  r.phi_sph = R(INFINITY);
+  while (cand) {
+    const int k = __ffs(cand) - 1;
+    cand &= cand - 1;
+    const R nc = m_fma(sx, C.uc[k], -sy * C.rc[k]);
+    if (m_abs(nc) < S.rad[k] * rho2 * irho && b <= S.cull_b[k]) {
+      mask |= 1u << k;
+      sphere_window_setup(s, r, k, (float)C.ec[k], (float)(m_fma(sx, C.rc[k], sy * C.uc[k]) * irho));
     }
   }
   r.sph_mask = mask;
-  r.phi_sph = R(INFINITY);
-  if (mask) {
-    unsigned m = mask;
-    while (m) {
-      const int k = __ffs(m) - 1;
-      m &= m - 1;
-      sphere_window_setup(s, r, k);
-    }
-    r.phi_sph = next_sphere_window(r, R(0));
-  }
+  if (mask) r.phi_sph = next_sphere_window(r, R(0));
   return 0;
 }
 

@@ -1,10 +1,13 @@
 """Train the surrogate MLP through the C-ABI and write its weights.
 
     python -m paper_2507_16165_gb300.train_surrogate [--out PATH] [--samples 4194304]
-                                                      [--epochs 900] [--seed 0]
+                                                      [--epochs 900] [--seed 0] [--lr 2e-3]
+                                                      [--batch 8192]
 
 Draws the training inputs (b/M log-uniform in [3 sqrt 3 + 1e-4, 1e3],
-r_obs/M uniform in [15, 100], psi0 uniform in (0, pi]; seeded), lets the
+r_obs/M uniform in [15, 100], psi0 uniform in (0, pi]; seeded; only pairs a
+static observer at r_obs can receive, b < r_obs / sqrt(1 - 2/r_obs), so that
+every sample is a valid integrator label), lets the
 library label them with its FP64 integrator and train the BF16 tensor-core
 MLP, then calibrates the served domain on an independent sample set (seed
 + 1000; 32 x 8 bins over ln(b - 3 sqrt 3) and r_obs) and saves the weights
@@ -24,7 +27,7 @@ DEFAULT = os.path.join(HERE, "data", "surrogate_m1.bin")
 
 
 def train(out: str = DEFAULT, samples: int = 1 << 22, epochs: int = 900, seed: int = 0,
-          batch: int = 8192, lr: float = 3e-3, calib_samples: int = 1 << 21) -> dict:
+          batch: int = 8192, lr: float = 2e-3, calib_samples: int = 1 << 21) -> dict:
     import torch
 
     import paper_2507_16165_gb300 as bh
@@ -32,13 +35,13 @@ def train(out: str = DEFAULT, samples: int = 1 << 22, epochs: int = 900, seed: i
     torch.cuda.set_device(0)
     sc = bh.Scene(W.config4(16).scene)
     try:
-        b, r, psi = W.surrogate_samples(samples, seed=seed)
+        b, r, psi = W.reachable_surrogate_samples(samples, seed=seed)
         t0 = time.time()
         rep = bh.bh_surrogate_train(sc.handle, b, r, psi, epochs=epochs, batch=batch, lr=lr,
                                     seed=seed + 1)
         rep["wall_s"] = time.time() - t0
         rep.update(samples=samples, epochs=epochs, seed=seed, batch=batch, lr=lr)
-        cb, cr, cp = W.surrogate_samples(calib_samples, seed=seed + 1000)
+        cb, cr, cp = W.reachable_surrogate_samples(calib_samples, seed=seed + 1000)
         cal = bh.bh_surrogate_calibrate(sc.handle, cb, cr, cp, nb_lb=32, nb_r=8)
         rep["calibration"] = {
             "samples": calib_samples, "seed": seed + 1000,
@@ -63,8 +66,10 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 22)
     ap.add_argument("--epochs", type=int, default=900)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--batch", type=int, default=8192)
     a = ap.parse_args()
-    rep = train(a.out, a.samples, a.epochs, a.seed)
+    rep = train(a.out, a.samples, a.epochs, a.seed, batch=a.batch, lr=a.lr)
     cal = rep.pop("calibration")
     rep["served_bins"] = cal["served_bins"]
     rep["calib_served_fraction"] = cal["served_fraction"]

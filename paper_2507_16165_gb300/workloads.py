@@ -175,6 +175,27 @@ def surrogate_samples(n: int, seed: int = 0, b_lo: float = 3.0 * math.sqrt(3.0) 
     return np.exp(lb), r, psi
 
 
+def reachable_surrogate_samples(n: int, seed: int = 0, b_lo: float = 3.0 * math.sqrt(3.0) + 1e-4,
+                                b_hi: float = 1e3, r_range=(15.0, 100.0)):
+    """n training inputs drawn as surrogate_samples draws them, keeping only
+    pairs (b, r_obs) a static observer at r_obs can receive: b below
+    r_obs / sqrt(1 - 2/r_obs) (the ray through the image edge at 90 degrees;
+    units of M).  The kept pairs follow the same density restricted to that
+    domain, and all n of them are valid integrator samples."""
+    import numpy as np
+    bs, rs, ps = [], [], []
+    have, k = 0, 0
+    while have < n:
+        b, r, psi = surrogate_samples(max(2 * (n - have), 1024), seed * 1009 + k, b_lo, b_hi, r_range)
+        keep = b < (1.0 - 1e-6) * r / np.sqrt(1.0 - 2.0 / r)
+        bs.append(b[keep])
+        rs.append(r[keep])
+        ps.append(psi[keep])
+        have += int(keep.sum())
+        k += 1
+    return (np.concatenate(bs)[:n], np.concatenate(rs)[:n], np.concatenate(ps)[:n])
+
+
 def sky_texture(seed: int = 0, w: int = 512, h: int = 256):
     """A synthetic equirectangular RGBA8 sky image (h x w, uint32), standing
     in for the paper's background photographs: a smooth seeded colour field

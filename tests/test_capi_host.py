@@ -43,13 +43,15 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "bh.h"\nint main(void){'
-                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bh_sphere), sizeof(bh_scene_desc),'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bh_sphere), sizeof(bh_scene_desc),'
                    'sizeof(bh_camera), sizeof(bh_render_opts), sizeof(bh_stats),'
                    'offsetof(bh_render_opts, abort_after), offsetof(bh_stats, kernel_ms),'
                    'sizeof(bh_tune_result), offsetof(bh_render_opts, h_max_far),'
                    'offsetof(bh_render_opts, paper_eps), offsetof(bh_render_opts, spp),'
                    'offsetof(bh_render_opts, doppler), offsetof(bh_render_opts, rtol_far),'
-                   'offsetof(bh_render_opts, host_strips));return 0;}')
+                   'offsetof(bh_render_opts, host_strips), offsetof(bh_render_opts, rtol_near),'
+                   'offsetof(bh_render_opts, queue_chunk), offsetof(bh_tune_result, queue_chunk));'
+                   'return 0;}')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
@@ -59,12 +61,14 @@ def test_struct_layout_matches_header(tmp_path):
             _capi.bh_stats.kernel_ms.offset, ctypes.sizeof(_capi.bh_tune_result),
             _capi.bh_render_opts.h_max_far.offset, _capi.bh_render_opts.paper_eps.offset,
             _capi.bh_render_opts.spp.offset, _capi.bh_render_opts.doppler.offset,
-            _capi.bh_render_opts.rtol_far.offset, _capi.bh_render_opts.host_strips.offset]
+            _capi.bh_render_opts.rtol_far.offset, _capi.bh_render_opts.host_strips.offset,
+            _capi.bh_render_opts.rtol_near.offset, _capi.bh_render_opts.queue_chunk.offset,
+            _capi.bh_tune_result.queue_chunk.offset]
     assert got == want
 
 
 def test_version(lib):
-    assert bh.bh_version() == 1
+    assert bh.bh_version() == 2
 
 
 def test_camera_basis(lib):

@@ -49,7 +49,51 @@ def _rand_params(seed):
     return mlp.pack(d).astype(np.float32)
 
 
+# Element-wise allowances.  Both sides round the same values to BF16 (weights;
+# back-propagated gradients; activations as BF16 high + low pairs); they
+# differ by the kernels' SiLU, evaluated from the hardware tanh (relative
+# error about 2^-11), and by FP32 accumulation.  A value that the two sides
+# compute a hair apart may round to neighbouring BF16 numbers: one BF16
+# spacing, at most 2^-7 of the value.  Each gradient element is a sum of
+# products, so it is held to a multiple of the same sum taken over absolute
+# values (the products' magnitudes, back-propagated through |W| and
+# |SiLU'|): GRAD_ALLOW covers one BF16 spacing in each product plus the
+# tanh error compounded over the three hidden layers.  Forward outputs carry
+# no BF16 rounding of their own (activations enter as exact-to-2^-16
+# pairs), only the tanh error: INFER_ALLOW of the absolute-value sum.
+GRAD_ALLOW = 3 * 2.0 ** -7
+INFER_ALLOW = 8 * 2.0 ** -11
+
+
+def _abs_bounds(p, x, t):
+    """Absolute-value sums of the forward products (per output) and of the
+    backward products (per parameter) of the reference network."""
+    _, c = mlp.forward(p.astype(np.float64), x.astype(np.float64), use_bf16=True)
+    W = [np.abs(w) for w in c["W"]]
+    P = mlp.unpack(p.astype(np.float64))
+    n = len(x)
+    # forward: |X||W1| + |b1| ... through |SiLU| (|SiLU(z)| <= |z|)
+    A = np.abs(c["X"]) @ W[0] + np.abs(P["b1"])
+    for k in (1, 2, 3):
+        A = A @ W[k] + np.abs(P["b%d" % (k + 1)])
+    fwd = A[:, :mlp.NOUT]
+    # backward: |dZ| propagated through |W|^T and |SiLU'|
+    y, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), use_bf16=True)
+    dZ = np.zeros((n, mlp.NO))
+    dZ[:, :mlp.NOUT] = np.abs(2.0 * (y - t) / (n * mlp.NOUT))
+    g = {"W4": np.abs(c["H3"]).T @ dZ, "b4": dZ.sum(0)}
+    for k, (H, Z) in zip((3, 2, 1), (("H2", "Z3"), ("H1", "Z2"), ("X", "Z1"))):
+        dZ = (dZ @ W[k].T) * np.abs(mlp.silu_grad(c[Z]))
+        g["W%d" % k] = np.abs(c[H]).T @ dZ
+        g["b%d" % k] = dZ.sum(0)
+    return fwd, mlp.pack(g)
+
+
 def test_training_gradients_match_fp64_reference():
+    """bh_mlp_grad element by element against the FP64 reference on the
+    same BF16-rounded values (GRAD_ALLOW of each element's absolute-value
+    sum), outputs likewise (INFER_ALLOW); and close to the exact FP64
+    gradient in norm."""
     rng = np.random.default_rng(5)
     p = _rand_params(6)
     x = np.zeros((256, 16), np.float32)
@@ -57,24 +101,31 @@ def test_training_gradients_match_fp64_reference():
     t = rng.normal(0, 1, (256, 3)).astype(np.float32)
     y, g, loss = bh.bh_mlp_grad(p, x, t)
     loss_r, g_r, y_r = mlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t, use_bf16=True)
-    assert np.linalg.norm(y - y_r) <= 1e-2 * np.linalg.norm(y_r)
+    fwd, gabs = _abs_bounds(p, x, t)
+    assert np.all(np.abs(y - y_r) <= INFER_ALLOW * fwd + 1e-6)
     assert abs(loss - loss_r) <= 1e-2 * loss_r
-    for name, blk in mlp.unpack(g).items():
-        ref = mlp.unpack(g_r)[name]
-        assert np.linalg.norm(blk - ref) <= 2e-2 * np.linalg.norm(ref) + 1e-7, name
+    err = np.abs(g - g_r)
+    bound = GRAD_ALLOW * gabs + 1e-9
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), float((err / bound).max()))
     # the BF16 path stays close to the exact FP64 gradient too
     _, g_exact, _ = mlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t)
     assert np.linalg.norm(g - g_exact) <= 5e-2 * np.linalg.norm(g_exact)
 
 
 def test_inference_path_matches_fp64_reference():
+    """The render's inference path (fragment-ordered weights, warp MLP)
+    element by element against the FP64 reference (INFER_ALLOW of each
+    output's absolute-value sum)."""
     rng = np.random.default_rng(7)
     p = _rand_params(8)
     x = np.zeros((1000, 16), np.float32)
     x[:, :mlp.NFEAT] = rng.uniform(-1, 1, (1000, mlp.NFEAT))
     y = bh.bh_mlp_infer(p, x)
     y_r, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), use_bf16=True)
-    assert np.linalg.norm(y - y_r) <= 2e-2 * np.linalg.norm(y_r)
+    fwd, _ = _abs_bounds(p, x, np.zeros((1000, 3)))
+    err = np.abs(y - y_r)
+    assert np.all(err <= INFER_ALLOW * fwd + 1e-6), float((err / (INFER_ALLOW * fwd + 1e-6)).max())
 
 
 WEIGHTS = os.path.join(os.path.dirname(bh.__file__), "data", "surrogate_m1.bin")
@@ -188,30 +239,65 @@ def test_calibration_table_matches_its_definition(trained):
     bh.bh_surrogate_load(sc.handle, WEIGHTS)   # restore the shipped table
 
 
-def test_network_saves_integration_steps(trained):
-    """What the network gains: every ray it serves is finished without
-    integration, so the surrogate render takes fewer integrator steps than
-    the mixed-precision render of the same image, by about the steps those
-    rays would have cost, while the image agrees (checked in the parity
-    test below)."""
+def _timed_render(sc, cams, mode, reps=5, **kw):
+    """Median device time (CUDA events) of renders of one frame, and stats."""
     import torch
-    w, sc = trained
-    sc.render(w.cameras, "mixed", rtol=1e-5, atol=1e-7)
-    torch.cuda.synchronize()
+    cam = cams[0]
+    n = cam.w * cam.h
+    f64 = mode == "fp64"
+    dirs = torch.empty(2 * n, dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    flags = torch.empty(n, dtype=torch.int16, device="cuda")
+    rgba = torch.empty(n, dtype=torch.int32, device="cuda")
+    c = sc.cameras(cams)
+    stream = torch.cuda.Stream()
+    opts = bh.render_opts(mode, stream, **kw)
+    ms = []
+    for i in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bh.bh_render(sc.handle, c, [cam.w], [cam.h], dirs, flags, rgba, opts)
+        e.record(stream)
+        stream.synchronize()
+        if i:
+            ms.append(a.elapsed_time(e))
     bh.bh_scene_sync(sc.handle)
-    mixed = sc.stats()
-    out = sc.render(w.cameras, "surrogate", rtol=1e-5, atol=1e-7)
-    torch.cuda.synchronize()
-    bh.bh_scene_sync(sc.handle)
-    surr = sc.stats()
-    served = surr["n_surrogate"] / surr["rays"]
+    return float(np.median(ms)), sc.stats(), flags
+
+
+def test_network_gain_in_steps_and_time(trained):
+    """What the network gains, on the config-4 frame at 2048^2 (spheres
+    included): every ray it serves is finished without integration, so the
+    surrogate render takes fewer integrator steps than the mixed-precision
+    render of the same frame, by about the steps those rays would have
+    cost; in time it renders the frame far faster than the FP64 integrator
+    -- the paper's method in its own precision -- at its 1e-3 rad bound.
+    Against the FP32 / mixed integrator the network costs more time per
+    ray than the integration it saves (about 20 SM cycles of mma.sync per
+    ray against about 14 for the whole FP32 integration); the measured
+    ratio is printed, not asserted."""
+    w = W.config4(2048)
+    sc = bh.Scene(w.scene)
+    try:
+        bh.bh_surrogate_load(sc.handle, WEIGHTS)
+        t64, s64, _ = _timed_render(sc, w.cameras, "fp64", reps=2, rtol=1e-10, atol=1e-10)
+        tmx, smx, _ = _timed_render(sc, w.cameras, "mixed", rtol=1e-5, atol=1e-7)
+        tsu, ssu, flags = _timed_render(sc, w.cameras, "surrogate", rtol=1e-5, atol=1e-7)
+    finally:
+        sc.close()
+    n = w.n_rays
+    served = ssu["n_surrogate"] / n
     assert served > 0.3
-    total = mixed["steps"] + mixed["steps_fp64"]
-    saved = total - (surr["steps"] + surr["steps_fp64"])
+    assert int(((flags & bh.BH_FLAG_SURR) != 0).sum()) == ssu["n_surrogate"]
+    total = smx["steps"]
+    saved = total - ssu["steps"]
     # served rays are the cheaper ones (far from the photon sphere), so the
     # saving is a positive share of the steps but below the served share
     assert saved > 0.2 * served * total
-    assert int(((out["flags"] & bh.BH_FLAG_SURR) != 0).sum()) == surr["n_surrogate"]
+    assert tsu < t64 / 5.0
+    print(f"\nnetwork gain at 2048^2: served {served:.3f}, steps {total} -> {ssu['steps']}; "
+          f"FP64 {t64:.3f} ms, mixed {tmx:.3f} ms, surrogate {tsu:.3f} ms "
+          f"(x{t64 / tsu:.1f} over FP64, x{tmx / tsu:.2f} of mixed)")
 
 
 @pytest.mark.parametrize("spheres", [False, True])
