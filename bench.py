@@ -379,6 +379,7 @@ class FormRun:
         tanh per hidden activation loads, with its tensor-pipe work beside."""
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         if self.form == "surrogate":
+            # kernel_ms[0]: the band pre-pass and the surrogate pass
             t_ms = sum(km[0] for km in kernel_ms)
             mufu = tot["mlp_rays"] * MLP_MUFU_PER_RAY
             peak = SM_COUNT * MUFU_PER_SM * sm_max * 1e6 / 1e12
@@ -388,7 +389,7 @@ class FormRun:
             return {
                 "bound": "xu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_surrogate (MLP by mma.sync BF16 + integrator fallback)",
+                "kernel": "k_surrogate (set-up, MLP by mma.sync BF16, shading of the served rays)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM} MUFU ops per cycle x "
                                f"{sm_max:.0f} MHz (max SM clock)",
                 "algorithmic": f"{MLP_MUFU_PER_RAY} tanh per network evaluation x "

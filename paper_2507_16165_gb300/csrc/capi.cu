@@ -640,7 +640,19 @@ extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int 
     if (e == cudaSuccess) e = launch_render(pr.p, pr.kmode, lb, sc->side, nullptr);
     if (e == cudaSuccess) e = cudaEventRecord(sc->join, sc->side);
   }
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+  // MIXED: the strips without band pixels first, so the copy stream has their
+  // outputs to move while the FP64 band pass finishes; then those with band
+  // pixels, whose copies wait for it
+  int order[BH_MAX_HOST_STRIPS];
+  bool banded[BH_MAX_HOST_STRIPS];
+  int no = 0;
+  for (int k = 0; k < ns; ++k) banded[k] = mixed && strip_has_band(sc, n_cams, strips[k]);
+  for (int k = 0; k < ns; ++k)
+    if (!banded[k]) order[no++] = k;
+  for (int k = 0; k < ns; ++k)
+    if (banded[k]) order[no++] = k;
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+    const int k = order[i];
     const HostStrip& t = strips[k];
     Params ps = pr.p;
     ps.q_begin = t.q_lo;
@@ -658,12 +670,11 @@ extern "C" int bh_render_host(const bh_scene* scene, const bh_camera* cams, int 
     }
     // the strip's queue counters (the band pass's run on beside it);
     // statistics and status over the frame
-    if (k > 0) e = cudaMemsetAsync(sc->d_ws, 0, offsetof(WorkK, band_count), stream);
+    if (i > 0) e = cudaMemsetAsync(sc->d_ws, 0, offsetof(WorkK, band_count), stream);
     if (e == cudaSuccess) e = launch_render(ps, pr.kmode, ls, stream, nullptr);
     if (e == cudaSuccess) e = cudaEventRecord(sc->strip_ev[k], stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sc->copy, sc->strip_ev[k], 0);
-    if (e == cudaSuccess && mixed && strip_has_band(sc, n_cams, t))
-      e = cudaStreamWaitEvent(sc->copy, sc->join, 0);
+    if (e == cudaSuccess && banded[k]) e = cudaStreamWaitEvent(sc->copy, sc->join, 0);
     if (e == cudaSuccess) e = copy_range(t.o_lo, t.o_hi, sc->copy);
   }
   if (mixed && e == cudaSuccess) e = cudaStreamWaitEvent(stream, sc->join, 0);

@@ -19,6 +19,18 @@ namespace bhk {
 // ---------------------------------------------------------------------------
 // Precision-overloaded math.
 // ---------------------------------------------------------------------------
+// Square root.  sqrt_approx is the single-instruction hardware
+// approximation (relative error about 2^-23, far inside the FP32 passes'
+// 1e-4 rad budget; 0 gives 0, a negative argument NaN), used in the FP32
+// arccos, the sphere windows and the warp's sphere cull; m_sqrt keeps the
+// correctly rounded routine (in the mixed tile pass the approximation there
+// measured 5% slower: the pass sits at its register limit and the changed
+// code spilled more).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
@@ -129,7 +141,7 @@ __device__ __forceinline__ float m_acos(float x) {
   p = fmaf(a, p, 0.0889789874f);
   p = fmaf(a, p, -0.2145988016f);
   p = fmaf(a, p, 1.5707963050f);
-  const float r = sqrtf(1.0f - a) * p;
+  const float r = sqrt_approx(1.0f - a) * p;
   return x < 0.0f ? 3.14159265358979324f - r : r;
 }
 __device__ __forceinline__ float m_asin(float x) {
@@ -442,7 +454,7 @@ __device__ __forceinline__ void sphere_window_setup(const SceneK& s, Ray<R>& r, 
   float pc = m_atan2(cy, cx);
   if (pc < 0.0f) pc += 6.28318530717958647692f;
   r.win->c[k] = pc;
-  r.win->d[k] = m_asin(fminf(1.0f, sqrtf(rp2 * rcp_approx(rho2)))) + 1e-4f;
+  r.win->d[k] = m_asin(fminf(1.0f, sqrt_approx(rp2 * rcp_approx(rho2)))) + 1e-4f;
 }
 
 // The first window of sphere k whose end lies at or after phi_from:
@@ -485,12 +497,12 @@ __device__ __forceinline__ unsigned warp_sphere_candidates(const SceneK& s, cons
   const float x0 = __shfl_sync(full, fx, 0), y0 = __shfl_sync(full, fy, 0);
   const float dx = fx - x0, dy = fy - y0;
   const float d2 = fmaf(dx, dx, dy * dy);
-  const float dmax = sqrtf(__uint_as_float(__reduce_max_sync(full, __float_as_uint(d2))));
+  const float dmax = sqrt_approx(__uint_as_float(__reduce_max_sync(full, __float_as_uint(d2))));
   const float reach = fmaf(dmax + cam.f.pdiag, 1.0001f, 1e-5f);
   const int k = threadIdx.x & 31;
   bool maybe = false;
   if (k < s.n_sph) {
-    const float rho0 = sqrtf(fmaf(x0, x0, y0 * y0));
+    const float rho0 = sqrt_approx(fmaf(x0, x0, y0 * y0));
     const float g = fabsf(fmaf(x0, cam.f.uc[k], -y0 * cam.f.rc[k])) - s.f.rad[k] * rho0;
     maybe = g <= (s.f.cnorm[k] + s.f.rad[k]) * reach;
   }
