@@ -288,10 +288,12 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   }
   r.phi_evt = m_min(m_min(r.phi_node, r.phi_sph), tol.phi_max);
   r.steps = 0;
-  // FP64 mirrors the oracle's starting step; FP32 starts at the step cap
-  // (the controller shrinks it when the first attempt is rejected)
-  r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01)) : tol.h_max;
-  // far FP32 rays may take longer steps; they still start at h_max
+  // FP64 mirrors the oracle's starting step; FP32 starts at the ray's step
+  // cap, h_far for far rays (the controller shrinks it when the first
+  // attempt is rejected; near the observer u is small and the long first
+  // step is accepted: 5.27 -> 4.84 attempted steps per ray at 4096^2)
+  r.h = d64 ? initial_step<R>(SR<R>(p.s).M3, r.u, r.v, tol.rtol, tol.atol, R(0.01))
+            : (far ? tol.h_far : tol.h_max);
   if (far) r.aux |= kAuxFar;
   // the FP32 form's near-critical rays, which the other forms integrate in
   // FP64, are held to rtol_near
