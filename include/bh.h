@@ -303,8 +303,10 @@ int bh_render_stats(const bh_scene *scene, bh_stats *out);
  * the azimuth of the first disk node in the orbital plane -- to the
  * deflection delta = phi_inf - alpha (alpha: the flat-space exit angle) and
  * u b at the disk nodes psi0 and psi0 + pi: 3 inputs, 3 hidden layers of 64
- * with SiLU, 3 outputs; BF16 operands with FP32 accumulation on the tensor
- * cores for training and inference, FP32 master weights and Adam.  It is
+ * with SiLU, 3 outputs; tensor-core operands with FP32 accumulation: BF16
+ * in training (FP32 master weights and Adam), the trained BF16 weight values
+ * held exactly in FP16 for inference, whose activations enter as FP16
+ * high + low pairs.  It is
  * trained on labels the FP64 integrator computes, and calibrated on held-
  * out samples: per bin of (ln(b - 3 sqrt 3 M), r_obs) the 99.9th-percentile
  * error decides whether BH_MODE_SURROGATE may answer rays there.  Rays in
@@ -398,8 +400,9 @@ int bh_surrogate_load(bh_scene *scene, const char *path);
  * Synchronous. */
 int bh_mlp_grad(const float *params, int n, const float *x, const float *t, float *y,
                 float *grad, float *loss, void *stream);
-/* The render's inference path (fragment-ordered BF16 weights, warp MLP) on
- * host feature rows x[n][16] -> y[n][3].  Synchronous. */
+/* The render's inference path (fragment-ordered weights: the parameters'
+ * BF16 values held in FP16; warp MLP) on host feature rows x[n][16] ->
+ * y[n][3].  Synchronous. */
 int bh_mlp_infer(const float *params, int n, const float *x, float *y, void *stream);
 
 /* ---- batched launch in a CUDA graph, autotuning ------------------------

@@ -352,10 +352,16 @@ std::vector<float> init_params(uint64_t seed) {
   return p;
 }
 
-// B-operand fragments of the inference MLP from FP32 masters.
+// B-operand fragments of the inference MLP from FP32 masters: the BF16
+// weights the network was trained with, held in FP16 (every BF16 value in
+// FP16's range is an FP16 value), those of the hidden layers and their
+// biases halved so the kernel's accumulators hold z / 2.
 void pack_fragments(const std::vector<float>& p, std::vector<uint2>* frag, std::vector<float>* bias) {
   frag->assign(bhs::NFRAG, uint2{0u, 0u});
-  auto bits = [](float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
+  float scale = 0.5f;
+  auto bits = [&](float x) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(scale * __bfloat162float(__float2bfloat16_rn(x))));
+  };
   auto layer = [&](int off, int fr, int KB, int NJ, int ld) {
     for (int kb = 0; kb < KB; ++kb)
       for (int j = 0; j < NJ; ++j)
@@ -371,12 +377,13 @@ void pack_fragments(const std::vector<float>& p, std::vector<uint2>* frag, std::
   layer(bhs::OW1, bhs::FR1, 1, 8, bhs::HID);
   layer(bhs::OW2, bhs::FR2, 4, 8, bhs::HID);
   layer(bhs::OW3, bhs::FR3, 4, 8, bhs::HID);
+  scale = 1.0f;
   layer(bhs::OW4, bhs::FR4, 4, 1, bhs::NO);
   bias->assign(bhs::NBIAS, 0.0f);
   for (int n = 0; n < bhs::HID; ++n) {
-    (*bias)[n] = p[bhs::OB1 + n];
-    (*bias)[bhs::HID + n] = p[bhs::OB2 + n];
-    (*bias)[2 * bhs::HID + n] = p[bhs::OB3 + n];
+    (*bias)[n] = 0.5f * p[bhs::OB1 + n];
+    (*bias)[bhs::HID + n] = 0.5f * p[bhs::OB2 + n];
+    (*bias)[2 * bhs::HID + n] = 0.5f * p[bhs::OB3 + n];
   }
   for (int n = 0; n < 8; ++n) (*bias)[3 * bhs::HID + n] = p[bhs::OB4 + n];
 }

@@ -3,6 +3,7 @@
     python -m paper_2507_16165_gb300.train_surrogate [--out PATH] [--samples 4194304]
                                                       [--epochs 900] [--seed 0] [--lr 2e-3]
                                                       [--batch 8192]
+    python -m paper_2507_16165_gb300.train_surrogate --recalibrate [--out PATH] [--seed 0]
 
 Draws the training inputs (b/M log-uniform in [3 sqrt 3 + 1e-4, 1e3],
 r_obs/M uniform in [15, 100], psi0 uniform in (0, pi]; seeded; only pairs a
@@ -14,6 +15,11 @@ MLP, then calibrates the served domain on an independent sample set (seed
 and calibration table (bh_surrogate_save) with a JSON report next to them
 that includes the per-bin 99.9th-percentile errors.  The weights are
 for M = 1 units and any scene mass (inputs and outputs are scaled by M).
+
+--recalibrate keeps the saved weights and redoes only the calibration (the
+same seed + 1000 sample set) with the library's current inference path,
+rewriting the table in the weights file and the calibration section of its
+JSON report.
 """
 from __future__ import annotations
 
@@ -41,21 +47,52 @@ def train(out: str = DEFAULT, samples: int = 1 << 22, epochs: int = 900, seed: i
                                     seed=seed + 1)
         rep["wall_s"] = time.time() - t0
         rep.update(samples=samples, epochs=epochs, seed=seed, batch=batch, lr=lr)
-        cb, cr, cp = W.reachable_surrogate_samples(calib_samples, seed=seed + 1000)
-        cal = bh.bh_surrogate_calibrate(sc.handle, cb, cr, cp, nb_lb=32, nb_r=8)
-        rep["calibration"] = {
-            "samples": calib_samples, "seed": seed + 1000,
+        rep["calibration"] = _calibrate(bh, W, sc, seed, calib_samples)
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        bh.bh_surrogate_save(sc.handle, out)
+        with open(os.path.splitext(out)[0] + ".json", "w") as f:
+            json.dump(rep, f, indent=1)
+        return rep
+    finally:
+        sc.close()
+
+
+def _calibrate(bh, W, sc, seed: int, calib_samples: int) -> dict:
+    cb, cr, cp = W.reachable_surrogate_samples(calib_samples, seed=seed + 1000)
+    cal = bh.bh_surrogate_calibrate(sc.handle, cb, cr, cp, nb_lb=32, nb_r=8)
+    return {"samples": calib_samples, "seed": seed + 1000,
             "served_fraction": cal["served_fraction"],
             "served_bins": int(cal["served"].sum()),
             "p999_delta": cal["p999_delta"].round(7).tolist(),
             "p999_r": cal["p999_r"].round(7).tolist(),
             "counts": cal["counts"].tolist(),
             "served": cal["served"].astype(int).tolist()}
-        os.makedirs(os.path.dirname(out), exist_ok=True)
+
+
+def recalibrate(out: str = DEFAULT, seed: int = 0, calib_samples: int = 1 << 21) -> dict:
+    """Redo the calibration of saved weights with the current inference path."""
+    import torch
+
+    import paper_2507_16165_gb300 as bh
+    from paper_2507_16165_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    sc = bh.Scene(W.config4(16).scene)
+    try:
+        bh.bh_surrogate_load(sc.handle, out)
+        _, old = bh.bh_surrogate_get(sc.handle)
+        cal = _calibrate(bh, W, sc, seed, calib_samples)
         bh.bh_surrogate_save(sc.handle, out)
-        with open(os.path.splitext(out)[0] + ".json", "w") as f:
+        path = os.path.splitext(out)[0] + ".json"
+        rep = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                rep = json.load(f)
+        rep["calibration"] = cal
+        with open(path, "w") as f:
             json.dump(rep, f, indent=1)
-        return rep
+        _, new = bh.bh_surrogate_get(sc.handle)
+        return {"served_fraction": cal["served_fraction"], "served_bins": cal["served_bins"],
+                "table_changed_bins": int((old != new).sum())}
     finally:
         sc.close()
 
@@ -68,7 +105,11 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--recalibrate", action="store_true")
     a = ap.parse_args()
+    if a.recalibrate:
+        print(json.dumps(recalibrate(a.out, a.seed)))
+        return
     rep = train(a.out, a.samples, a.epochs, a.seed, batch=a.batch, lr=a.lr)
     cal = rep.pop("calibration")
     rep["served_bins"] = cal["served_bins"]

@@ -59,8 +59,10 @@ def _rand_params(seed):
 # values (the products' magnitudes, back-propagated through |W| and
 # |SiLU'|): GRAD_ALLOW covers one BF16 spacing in each product plus the
 # tanh error compounded over the three hidden layers.  Forward outputs carry
-# no BF16 rounding of their own (activations enter as exact-to-2^-16
-# pairs), only the tanh error: INFER_ALLOW of the absolute-value sum.
+# no rounding of their own beyond the weights' (training: activations enter
+# as BF16 pairs exact to 2^-16; inference: the same BF16 weight values held
+# in FP16, activations as FP16 pairs exact to about 2^-22), only the tanh error:
+# INFER_ALLOW of the absolute-value sum.
 GRAD_ALLOW = 3 * 2.0 ** -7
 INFER_ALLOW = 8 * 2.0 ** -11
 
@@ -114,9 +116,9 @@ def test_training_gradients_match_fp64_reference():
 
 
 def test_inference_path_matches_fp64_reference():
-    """The render's inference path (fragment-ordered weights, warp MLP)
-    element by element against the FP64 reference (INFER_ALLOW of each
-    output's absolute-value sum)."""
+    """The render's inference path (fragment-ordered FP16 weights, warp MLP)
+    element by element against the FP64 reference on the BF16-rounded
+    weights (INFER_ALLOW of each output's absolute-value sum)."""
     rng = np.random.default_rng(7)
     p = _rand_params(8)
     x = np.zeros((1000, 16), np.float32)
