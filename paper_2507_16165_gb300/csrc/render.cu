@@ -811,11 +811,13 @@ __global__ void __launch_bounds__(512, kMinBlocks<R>) k_coherent(const __grid_co
 // FP32 integrator's list pass finishes after this pass: with the integrator
 // inline, the pass's code outgrew the instruction cache and its warps waited
 // on instruction fetch for most of their cycles.
-// 128-thread blocks, three per SM, at most 144 registers a thread: the
-// three blocks (55,296 registers) and the FP64 band pass's four 64-register
-// warps (8,192) fit in an SM's 65,536 together, so the band pass runs beside
-// this pass instead of after it.
-__global__ void __maxnreg__(144) k_surrogate(const __grid_constant__ Params p) {
+// 128-thread blocks, four per SM, at most 112 registers a thread (no
+// spills): the four blocks (57,344 registers) and the FP64 band pass's four
+// 64-register warps (8,192) fill an SM's 65,536 together, so the band pass
+// runs beside this pass instead of after it.  The pass is latency-bound;
+// four blocks instead of three at 144 registers: 2.06 -> 1.94 ms per 4096^2
+// frame.
+__global__ void __maxnreg__(112) k_surrogate(const __grid_constant__ Params p) {
   __shared__ uint2 s_frag[bhs::NFRAG];
   __shared__ float s_bias[bhs::NBIAS];
   __shared__ float s_feat[4][32 * bhs::K0];  // feature rows of each warp
@@ -1275,7 +1277,7 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
   kb<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
   if (ls.band_ev) record(ls.band_ev[1], ls.side);
   cudaEventRecord(ls.join, ls.side);
-  k_surrogate<<<ls.num_sms * 3, 128, 0, stream>>>(p);
+  k_surrogate<<<ls.num_sms * 4, 128, 0, stream>>>(p);
   // the integrator finishes the rays the network did not answer; it follows
   // in stream order (as a programmatic dependent its waiting blocks would
   // take the SM room the FP64 band pass runs in)
