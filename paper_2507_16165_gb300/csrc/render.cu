@@ -493,7 +493,8 @@ template <typename R, int MODE>
 __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit, LocalStats& st) {
   const SceneR<R>& S = SR<R>(p.s);
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
-  R un, vn, fn, err2;
+  R un, vn, fn;
+  float err2;
   dp5_attempt<R>(S.M3, r.u, r.v, r.f, r.h, tol.rtol, tol.atol, un, vn, fn, err2);
   // rays far from the critical impact parameter (FP32 passes) are held to
   // rtol_far, the FP32 form's near-critical rays to rtol_near, atol scaled
@@ -509,7 +510,7 @@ __device__ __forceinline__ bool advance(const Params& p, Ray<R>& r, Hit<R>& hit,
   const R h = r.h;
   r.h = h * step_factor<R>(err2);
   r.h = m_min(r.h, MODE == MODE_FP32 ? r.hc : ((!d64 && (r.aux & kAuxFar)) ? tol.h_far : tol.h_max));
-  if (!(err2 <= R(1))) {
+  if (!(err2 <= 1.0f)) {
     st.c[ST_REJ]++;
     if (r.steps >= p.max_steps) {
       hit.flags = BH_FLAG_STEP_LIMIT;

@@ -65,11 +65,12 @@ __global__ void k_labels(int n, double M, const double* __restrict__ bs, const d
   bool esc = false, got_a = false, got_b = false;
   int st = 3;
   for (int steps = 0; steps < 100000 && phi < 64.0; ++steps) {
-    double un, vn, fn, err2;
+    double un, vn, fn;
+    float err2;
     dp5_attempt<double>(M3, u, v, f, h, rtol, rtol, un, vn, fn, err2);
     const double hs = h;
     h = hs * step_factor<double>(err2);
-    if (!(err2 <= 1.0)) continue;
+    if (!(err2 <= 1.0f)) continue;
     const double pb = phi + hs;
     Hermite<double> H;
     H.make(phi, hs, u, v, f, un, vn, fn);

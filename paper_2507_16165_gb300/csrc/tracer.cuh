@@ -239,9 +239,15 @@ __device__ __forceinline__ R accel(R M3, R u) {
 // One attempted step.  Returns the fifth-order state (un, vn), the FSAL
 // derivative fn = accel(un), and the squared Hairer error norm
 // err2 = ((eu/su)^2 + (ev/sv)^2) / 2 with su = atol + rtol max(|u|, |un|).
+// The error estimate (eu, ev) is formed in the working precision (it is a
+// small difference of stage sums); its normalisation and err2 are FP32 for
+// both types: err2 only steers the step size, which the FP32 step factor
+// already perturbs at 1e-7 relative, and decides acceptance, which a 1e-7
+// relative change of err2 can flip only within 1e-7 of err2 = 1.  In FP64
+// that takes the norm from 14 operations on the FP64 pipe to 6 conversions.
 template <typename R>
 __device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R atol,
-                                            R& un, R& vn, R& fn, R& err2) {
+                                            R& un, R& vn, R& fn, float& err2) {
   const R hv = h * v, h2 = h * h;
   const R F2 = accel(M3, m_fma(R(DP_C2), hv, u));
   const R F3 = accel(M3, m_fma(h2, R(DP_AB31) * f1, m_fma(R(DP_C3), hv, u)));
@@ -260,10 +266,11 @@ __device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R
                 m_fma(R(DP_EH3), F3, R(DP_EH1) * f1))));
   const R ev = h * m_fma(R(DP_E7), fn, m_fma(R(DP_E6), F6, m_fma(R(DP_E5), F5,
                 m_fma(R(DP_E4), F4, m_fma(R(DP_E3), F3, R(DP_E1) * f1)))));
-  const R su = m_fma(rtol, m_max(m_abs(u), m_abs(un)), atol);
-  const R sv = m_fma(rtol, m_max(m_abs(v), m_abs(vn)), atol);
-  const R ru = eu * m_rcp(su), rv = ev * m_rcp(sv);
-  err2 = R(0.5) * m_fma(ru, ru, rv * rv);
+  const float rt = (float)rtol, at = (float)atol;
+  const float su = fmaf(rt, fmaxf(fabsf((float)u), fabsf((float)un)), at);
+  const float sv = fmaf(rt, fmaxf(fabsf((float)v), fabsf((float)vn)), at);
+  const float ru = (float)eu * rcp_approx(su), rv = (float)ev * rcp_approx(sv);
+  err2 = 0.5f * fmaf(ru, ru, rv * rv);
 }
 
 // Step-size factor 0.9 err^(-1/5) clamped to [0.2, 10], from err2 = err^2.
@@ -274,8 +281,8 @@ __device__ __forceinline__ void dp5_attempt(R M3, R u, R v, R f1, R h, R rtol, R
 // NaN propagates to fmaxf, which returns 0.2.  The 0.9 is folded into the
 // exponent as log2(0.9).
 template <typename R>
-__device__ __forceinline__ R step_factor(R err2) {
-  const float e2 = (float)err2;
+__device__ __forceinline__ R step_factor(float err2) {
+  const float e2 = err2;
   const float fac = ex2_approx(fmaf(-0.1f, lg2_approx(e2), -0.15200309344504997f));
   return R(fminf(10.0f, fmaxf(0.2f, fac)));
 }
