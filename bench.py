@@ -274,10 +274,12 @@ FORMS = {
     "c5_surrogate": ("surrogate", "c5", {},
                      "tests/test_gpu_batch.py::test_batch64_full_size_sampled_parity[surrogate]"),
 }
-# MLP work per evaluated ray (mlp.cuh): 304 mma.sync m16n8k16 per warp of 32
-# rays (BF16 high and low halves of every activation, 4 layers) x 4096 FLOP,
-# and one tanh.approx (one MUFU operation) per hidden activation, 3 x 64.
-MLP_FLOP_PER_RAY = 304 * 4096 // 32
+# MLP work per evaluated ray (mlp_tc.cuh): per 128 rays, 18 tcgen05.mma of
+# M = 128, N = 64, K = 16 (the high and low halves of the inputs of layers
+# 1-3, four K blocks for layers 2 and 3) and 8 of N = 16 (layer 4), 2 FLOP a
+# multiply-add; and one tanh.approx (one MUFU operation) per hidden
+# activation, 3 x 64.
+MLP_FLOP_PER_RAY = 2 * (18 * 64 * 16 + 8 * 16 * 16)
 MLP_MUFU_PER_RAY = 3 * 64
 # special-function (MUFU) operations per SM and cycle on Blackwell: 4 per
 # SM sub-partition
@@ -389,7 +391,7 @@ class FormRun:
             return {
                 "bound": "xu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_surrogate (set-up, MLP by mma.sync BF16, shading of the served rays)",
+                "kernel": "k_surrogate (set-up, MLP by tcgen05 FP16 into tensor memory, shading of the served rays)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM} MUFU ops per cycle x "
                                f"{sm_max:.0f} MHz (max SM clock)",
                 "algorithmic": f"{MLP_MUFU_PER_RAY} tanh per network evaluation x "

@@ -400,9 +400,10 @@ int bh_surrogate_load(bh_scene *scene, const char *path);
  * Synchronous. */
 int bh_mlp_grad(const float *params, int n, const float *x, const float *t, float *y,
                 float *grad, float *loss, void *stream);
-/* The render's inference path (fragment-ordered weights: the parameters'
- * BF16 values held in FP16; warp MLP) on host feature rows x[n][16] ->
- * y[n][3].  Synchronous. */
+/* The render's inference path (tcgen05 tensor-core MLP, 128 rows a CTA, the
+ * parameters' BF16 weight values held in FP16) on host feature rows
+ * x[n][16] -> y[n][3].  Synchronous.  BH_E_DEVICE if a layer's MMAs did
+ * not complete within the kernel's wait limit. */
 int bh_mlp_infer(const float *params, int n, const float *x, float *y, void *stream);
 
 /* ---- batched launch in a CUDA graph, autotuning ------------------------

@@ -223,7 +223,7 @@ struct Params {
   int* band_list;     // queue slots deferred to FP64 [n_queue]
   int band_lanes;       // lanes of a band-pass warp that take rays (1..32)
   // surrogate mode
-  const uint2* mlp_frag;       // fragment-ordered BF16 weights (bhs::NFRAG)
+  const uint16_t* mlp_w;       // FP16 W^T tiles of the tensor-core path (bhs::TC_NW)
   const float* mlp_bias;       // bhs::NBIAS
   const unsigned char* surr_table;  // served (1) / fallback (0) per calibration bin
   int surr_nb_lb, surr_nb_r;   // table dimensions: ln(b - b_c) bins x r_obs bins

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 #include "render.h"
 #include "tracer.cuh"
 
@@ -799,116 +800,155 @@ __global__ void __launch_bounds__(512, kMinBlocks<R>) k_coherent(const __grid_co
   if (MODE == MODE_MIXED) pdl_wait_primary();
 }
 
-// Surrogate pass.  One 32-ray tile per warp grab: set up each ray as the
-// MIXED coherent pass does (FP32 camera, orbital plane, impact parameter,
-// first disk-node angle psi0, periastron; band rays belong to the FP64 pass,
-// radial rays finish at once), decide whether the MLP may answer it --
-// no sphere cut by the orbital plane, inside the training domain, and a
-// calibration bin whose measured 99.9th-percentile error is within the
-// threshold -- run the MLP for the whole warp on the tensor cores and shade
-// the rays it answers: a served ray escapes at phi_inf = alpha + delta
-// unless the disk is met at psi0 or psi0 + pi first (u b from the MLP gives
-// the crossing radius).  The rays it does not answer go to a list that the
-// FP32 integrator's list pass finishes after this pass: with the integrator
-// inline, the pass's code outgrew the instruction cache and its warps waited
-// on instruction fetch for most of their cycles.
-// 128-thread blocks, four per SM, at most 112 registers a thread (no
-// spills): the four blocks (57,344 registers) and the FP64 band pass's four
-// 64-register warps (8,192) fill an SM's 65,536 together, so the band pass
-// runs beside this pass instead of after it.  The pass is latency-bound;
-// four blocks instead of three at 144 registers: 2.06 -> 1.94 ms per 4096^2
-// frame.
+// Surrogate pass.  A CTA of four warps takes 128 queue slots at a time (warp
+// w the 32-slot group g + 32w, one tile row of one camera): each thread sets
+// up its ray as the MIXED coherent pass does (FP32 camera, orbital plane,
+// impact parameter, first disk-node angle psi0, periastron; band rays
+// belong to the FP64 pass, radial rays finish at once) and decides whether
+// the MLP may answer it -- no sphere cut by the orbital plane, inside the
+// training domain, and a calibration bin whose measured 99.9th-percentile
+// error is within the threshold.  When any of the 128 may, the CTA
+// evaluates the network for all of them on the tensor cores (mlp_cta_tc:
+// tcgen05.mma into tensor memory) and shades the rays it answers: a served
+// ray escapes at phi_inf = alpha + delta unless the disk is met at psi0 or
+// psi0 + pi first (u b from the MLP gives the crossing radius).  The rays it
+// does not answer go to a list that the FP32 integrator's list pass
+// finishes after this pass.
+// 128-thread CTAs, four per SM (54 KB of shared memory and 64 tensor-memory
+// columns each), at most 112 registers a thread: the four CTAs (57,344
+// registers) and the FP64 band pass's four 64-register warps (8,192) fill
+// an SM's 65,536 together, so the band pass runs beside this pass.  A layer
+// that does not complete within its poll limit sets BH_STATUS_WATCHDOG and
+// ends the pass.
 __global__ void __maxnreg__(112) k_surrogate(const __grid_constant__ Params p) {
-  __shared__ uint2 s_frag[bhs::NFRAG];
-  __shared__ float s_bias[bhs::NBIAS];
-  __shared__ float s_feat[4][32 * bhs::K0];  // feature rows of each warp
-  for (int i = threadIdx.x; i < bhs::NFRAG; i += blockDim.x) s_frag[i] = p.mlp_frag[i];
-  for (int i = threadIdx.x; i < bhs::NBIAS; i += blockDim.x) s_bias[i] = p.mlp_bias[i];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bhs::TcSmem& s = *reinterpret_cast<bhs::TcSmem*>(smem_raw);
+  __shared__ unsigned long long s_grab;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  for (int i = tid; i < bhs::TC_NW / 8; i += 128)
+    reinterpret_cast<uint4*>(s.w)[i] = reinterpret_cast<const uint4*>(p.mlp_w)[i];
+  for (int i = tid; i < bhs::NBIAS; i += 128) s.bias[i] = p.mlp_bias[i];
+  if (tid < 32) bhs::tmem_alloc(bhs::smem_u32(&s.tmem), bhs::TC_COLS);
+  if (tid == 0) bhs::mbar_init(bhs::smem_u32(&s.mbar), 1);
+  bhs::tc_fence_before();
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  float* feat = s_feat[threadIdx.x >> 5];
+  bhs::tc_fence_after();
+  const uint32_t tmem = s.tmem;
+  uint32_t phase = 0;
   const SceneR<float>& S = p.s.f;
   const float M = S.M, iM = 1.0f / M;
   const float bc_m = 5.19615242270663188f;  // 3 sqrt 3: b_crit / M
+  // slots per CTA grab: the queue chunk rounded up to whole 128-slot groups
+  const unsigned long long grab = (unsigned long long)((p.chunk + 127) / 128 * 128);
   LocalStats st;
   st.zero();
-  for_each_grab(p, st, [&](long long q) {
-    Ray<float> r;
-    SphWin win;
-    r.win = &win;
-    float b = 0.0f;
-    bool active = setup_slot<float, MODE_MIXED, float, false, true>(p, q, r, st, &b);
-    bool serve = false;
-    float r_obs = 0.0f;
-    float f[bhs::K0];
-    for (int k = 0; k < bhs::K0; ++k) f[k] = 0.0f;
-    if (active) {
-      r_obs = 1.0f / r.u;  // the set-up state is u = 1 / r_obs
-      const float bm = b * iM, rm = r_obs * iM;
-      bool ok = r.sph_mask == 0 && bm > bc_m + 1e-4f && rm >= 15.0f && rm <= 100.0f &&
-                (!p.s.disk_on || r.phi_node < 4.0f);
-      if (ok) {
-        bhs::surrogate_features<float>(bm, rm, p.s.disk_on ? r.phi_node : bhs::P_C, f);
-        const int ib = min(p.surr_nb_lb - 1, max(0, (int)((f[0] + 1.0f) * 0.5f * p.surr_nb_lb)));
-        const int ir = min(p.surr_nb_r - 1, max(0, (int)((rm - 15.0f) * (1.0f / 85.0f) * p.surr_nb_r)));
-        ok = p.surr_table[ib * p.surr_nb_r + ir] != 0;
-      }
-      serve = ok;
+  bool failed = false;
+  for (;;) {
+    if (tid == 0) {
+      s_grab = (unsigned long long)p.q_begin + atomicAdd(&p.ws->q_next, grab);
+      st.c[ST_GRABS]++;
     }
-    if (__any_sync(kFull, serve)) {
-      if (lane == 0) st.c[ST_MLP] += 32;
-      for (int k = 0; k < bhs::K0; ++k) feat[lane * bhs::K0 + k] = f[k];
-      __syncwarp();
-      float o[3];
-      bhs::mlp_warp(s_frag, s_bias, feat, o);
-      __syncwarp();
-      if (serve) {
-        const float delta = fmaf(o[0], bhs::D_S, bhs::D_C) * 4.0f * M / b;
-        const float alpha =
-            3.14159265358979f - asinf(fminf(1.0f, b * sqrtf(1.0f - 2.0f * M / r_obs) / r_obs));
-        const float phi_inf = alpha + delta;
-        Hit<float> hit;
-        hit.flags = BH_FLAG_ESC;
-        hit.phi = phi_inf;
-        hit.u = 0.0f;
-        hit.v = 0.0f;
-        if (p.s.disk_on) {
-          const float pa = r.phi_node, pb = pa + 3.14159265358979f;
-          const float ua = o[1] / b, ub = o[2] / b;
-          if (pa < phi_inf && ua > 0.0f && 1.0f / ua >= S.r_in && 1.0f / ua <= S.r_out) {
-            hit.flags = BH_FLAG_DISK;
-            hit.phi = pa;
-            hit.u = ua;
-          } else if (pb < phi_inf && ub > 0.0f && 1.0f / ub >= S.r_in && 1.0f / ub <= S.r_out) {
-            hit.flags = BH_FLAG_DISK;
-            hit.phi = pb;
-            hit.u = ub;
-          } else if (phi_inf > pa + 6.2831853f) {
-            serve = false;  // a third node crossing: beyond what the MLP predicts
-          }
+    __syncthreads();
+    const unsigned long long base = s_grab;
+    __syncthreads();
+    if (base >= (unsigned long long)p.n_queue) break;
+    if (p.abort_after && base >= p.abort_after) {
+      if (tid == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_ABORTED);
+      break;
+    }
+    const unsigned long long end =
+        base + grab < (unsigned long long)p.n_queue ? base + grab : (unsigned long long)p.n_queue;
+    for (unsigned long long g = base; g < end; g += 128) {
+      const long long q = (long long)g + tid;
+      Ray<float> r;
+      SphWin win;
+      r.win = &win;
+      float b = 0.0f;
+      bool active = setup_slot<float, MODE_MIXED, float, false, true>(p, q, r, st, &b);
+      bool serve = false;
+      float r_obs = 0.0f;
+      float f[bhs::K0];
+#pragma unroll
+      for (int k = 0; k < bhs::K0; ++k) f[k] = 0.0f;
+      if (active) {
+        r_obs = 1.0f / r.u;  // the set-up state is u = 1 / r_obs
+        const float bm = b * iM, rm = r_obs * iM;
+        bool ok = r.sph_mask == 0 && bm > bc_m + 1e-4f && rm >= 15.0f && rm <= 100.0f &&
+                  (!p.s.disk_on || r.phi_node < 4.0f);
+        if (ok) {
+          bhs::surrogate_features<float>(bm, rm, p.s.disk_on ? r.phi_node : bhs::P_C, f);
+          const int ib = min(p.surr_nb_lb - 1, max(0, (int)((f[0] + 1.0f) * 0.5f * p.surr_nb_lb)));
+          const int ir = min(p.surr_nb_r - 1, max(0, (int)((rm - 15.0f) * (1.0f / 85.0f) * p.surr_nb_r)));
+          ok = p.surr_table[ib * p.surr_nb_r + ir] != 0;
+        }
+        serve = ok;
+      }
+      if (__syncthreads_or(serve)) {
+        if (tid == 0) st.c[ST_MLP] += 128;
+        float o[3];
+        const bool done = bhs::mlp_cta_tc(s, tmem, phase, f, o);
+        if (__syncthreads_or(!done)) {
+          failed = true;
+          serve = false;
         }
         if (serve) {
-          r.aux |= BH_FLAG_SURR;
-          finish_ray<float, float>(p, r, hit);
-          st.count_flag(hit.flags | r.aux);
-          st.c[ST_SURR]++;
-          active = false;
+          const float delta = fmaf(o[0], bhs::D_S, bhs::D_C) * 4.0f * M / b;
+          const float alpha =
+              3.14159265358979f - asinf(fminf(1.0f, b * sqrtf(1.0f - 2.0f * M / r_obs) / r_obs));
+          const float phi_inf = alpha + delta;
+          Hit<float> hit;
+          hit.flags = BH_FLAG_ESC;
+          hit.phi = phi_inf;
+          hit.u = 0.0f;
+          hit.v = 0.0f;
+          if (p.s.disk_on) {
+            const float pa = r.phi_node, pb = pa + 3.14159265358979f;
+            const float ua = o[1] / b, ub = o[2] / b;
+            if (pa < phi_inf && ua > 0.0f && 1.0f / ua >= S.r_in && 1.0f / ua <= S.r_out) {
+              hit.flags = BH_FLAG_DISK;
+              hit.phi = pa;
+              hit.u = ua;
+            } else if (pb < phi_inf && ub > 0.0f && 1.0f / ub >= S.r_in && 1.0f / ub <= S.r_out) {
+              hit.flags = BH_FLAG_DISK;
+              hit.phi = pb;
+              hit.u = ub;
+            } else if (phi_inf > pa + 6.2831853f) {
+              serve = false;  // a third node crossing: beyond what the MLP predicts
+            }
+          }
+          if (serve) {
+            r.aux |= BH_FLAG_SURR;
+            finish_ray<float, float>(p, r, hit);
+            st.count_flag(hit.flags | r.aux);
+            st.c[ST_SURR]++;
+            active = false;
+          }
         }
       }
-    }
-    // the rest go to the integrator's list: one atomic per warp
-    const unsigned fb = __ballot_sync(kFull, active);
-    if (fb) {
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&p.ws->surr_count, (unsigned long long)__popc(fb));
-      base = __shfl_sync(kFull, base, 0);
-      if (active) {
-        p.surr_list[base + __popc(fb & ((1u << lane) - 1u))] = (int)q;
-        st.c[ST_FALLBACK]++;
+      // the rest go to the integrator's list: one atomic per warp
+      const unsigned fb = __ballot_sync(kFull, active);
+      if (fb) {
+        unsigned long long lb = 0;
+        if (lane == 0) lb = atomicAdd(&p.ws->surr_count, (unsigned long long)__popc(fb));
+        lb = __shfl_sync(kFull, lb, 0);
+        if (active) {
+          p.surr_list[lb + __popc(fb & ((1u << lane) - 1u))] = (int)q;
+          st.c[ST_FALLBACK]++;
+        }
       }
+      if (failed) break;
     }
-  });
+    if (failed) break;
+  }
+  if (failed && tid == 0) atomicOr(&p.ws->status, (unsigned)BH_STATUS_WATCHDOG);
   st.flush(p.ws);
+  bhs::tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    bhs::tc_fence_after();
+    bhs::tmem_dealloc(tmem, bhs::TC_COLS);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1278,7 +1318,7 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
   kb<<<ls.band_warps * ls.num_sms, 32, 0, ls.side>>>(p);
   if (ls.band_ev) record(ls.band_ev[1], ls.side);
   cudaEventRecord(ls.join, ls.side);
-  k_surrogate<<<ls.num_sms * 4, 128, 0, stream>>>(p);
+  k_surrogate<<<ls.num_sms * 4, 128, sizeof(bhs::TcSmem), stream>>>(p);
   // the integrator finishes the rays the network did not answer; it follows
   // in stream order (as a programmatic dependent its waiting blocks would
   // take the SM room the FP64 band pass runs in)
@@ -1291,6 +1331,11 @@ cudaError_t launch_surrogate(const Params& p, const LaunchShape& ls, cudaStream_
   cudaStreamWaitEvent(stream, ls.join, 0);
   if (ev) record(ev[3], stream);
   return cudaGetLastError();
+}
+
+cudaError_t surrogate_kernel_setup() {
+  return cudaFuncSetAttribute(k_surrogate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(bhs::TcSmem));
 }
 
 cudaError_t launch_coherent_only(const Params& p, int mode, const LaunchShape& ls,

@@ -30,6 +30,10 @@ struct LaunchShape {
 cudaError_t launch_render(const Params& p, int mode, const LaunchShape& ls, cudaStream_t stream,
                           cudaEvent_t* ev);
 
+// The surrogate pass's dynamic shared memory (its tensor-core tiles): set
+// before its launches on a device.
+cudaError_t surrogate_kernel_setup();
+
 // Launch a surrogate render: band pre-pass, FP64 band pass on the side
 // stream, the surrogate pass (which lists the rays it does not answer), the
 // integrator's lock-step pass over that list and the long-ray pass.

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 #include "runtime.h"
 #include "tracer.cuh"
 
@@ -25,7 +26,7 @@ struct SurrogateState {
   std::vector<float> params;        // bhs::NPARAM, FP32 master weights
   int nb_lb = 0, nb_r = 0;          // calibration table dims
   std::vector<unsigned char> table; // served (1) / fallback (0)
-  uint2* d_frag = nullptr;
+  uint16_t* d_w = nullptr;
   float* d_bias = nullptr;
   unsigned char* d_table = nullptr;
   int* d_list = nullptr;            // fallback list
@@ -285,31 +286,69 @@ __global__ void k_gather(int B, const int* __restrict__ idx, const float* __rest
   for (int k = 0; k < bhs::NO; ++k) Tb[i * bhs::NO + k] = T[s * bhs::NO + k];
 }
 
-// Inference on feature rows x[n][K0] through the render's warp MLP.
-__global__ void __launch_bounds__(256) k_mlp_infer(int n, const float* __restrict__ x, const uint2* frag_g,
-                                                   const float* bias_g, float* __restrict__ y) {
-  __shared__ uint2 s_frag[bhs::NFRAG];
-  __shared__ float s_bias[bhs::NBIAS];
-  for (int i = threadIdx.x; i < bhs::NFRAG; i += blockDim.x) s_frag[i] = frag_g[i];
-  for (int i = threadIdx.x; i < bhs::NBIAS; i += blockDim.x) s_bias[i] = bias_g[i];
+// Inference on feature rows x[n][K0] on the tensor cores (tcgen05): one CTA
+// of 128 threads per 128 rows, persistent over the row groups.  A layer that
+// does not complete in time sets *status and ends the CTA's loop.
+__global__ void __launch_bounds__(128) k_mlp_infer_tc(int n, const float* __restrict__ x,
+                                                      const uint16_t* __restrict__ wtc,
+                                                      const float* __restrict__ bias_g,
+                                                      float* __restrict__ y, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bhs::TcSmem& s = *reinterpret_cast<bhs::TcSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < bhs::TC_NW / 8; i += 128)
+    reinterpret_cast<uint4*>(s.w)[i] = reinterpret_cast<const uint4*>(wtc)[i];
+  for (int i = tid; i < bhs::NBIAS; i += 128) s.bias[i] = bias_g[i];
+  if (tid < 32) bhs::tmem_alloc(bhs::smem_u32(&s.tmem), bhs::TC_COLS);
+  if (tid == 0) bhs::mbar_init(bhs::smem_u32(&s.mbar), 1);
+  bhs::tc_fence_before();
   __syncthreads();
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  const int lane = threadIdx.x & 31;
-  __shared__ float s_x[8][32 * bhs::K0];
-  float* xs = s_x[threadIdx.x >> 5];
-  for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < n; w += warps) {
-    const int i = w * 32 + lane;
-    for (int k = 0; k < bhs::K0; ++k) xs[lane * bhs::K0 + k] = i < n ? x[(size_t)i * bhs::K0 + k] : 0.0f;
-    __syncwarp();
+  bhs::tc_fence_after();
+  const uint32_t tmem = s.tmem;
+  uint32_t phase = 0;
+  for (long long g = blockIdx.x; g * 128 < n; g += gridDim.x) {
+    const long long i = g * 128 + tid;
+    float f[bhs::K0];
+#pragma unroll
+    for (int k = 0; k < bhs::K0; ++k) f[k] = i < n ? x[i * bhs::K0 + k] : 0.0f;
     float o[3];
-    bhs::mlp_warp(s_frag, s_bias, xs, o);
-    __syncwarp();
+    const bool ok = bhs::mlp_cta_tc(s, tmem, phase, f, o);
     if (i < n) {
       y[3 * i] = o[0];
       y[3 * i + 1] = o[1];
       y[3 * i + 2] = o[2];
     }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, 1u);
+      break;
+    }
   }
+  bhs::tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    bhs::tc_fence_after();
+    bhs::tmem_dealloc(tmem, bhs::TC_COLS);
+  }
+}
+
+// FP16 W^T tiles of the tensor-core path (the trained BF16 values, the
+// hidden layers' halved) from FP32 masters.
+void pack_tc_weights(const std::vector<float>& p, std::vector<uint16_t>* w) {
+  w->assign(bhs::TC_NW, 0);
+  auto h = [](float x, float sc) {
+    return (uint16_t)__half_as_ushort(__float2half_rn(sc * __bfloat162float(__float2bfloat16_rn(x))));
+  };
+  for (int n = 0; n < bhs::HID; ++n) {
+    for (int k = 0; k < bhs::K0; ++k)
+      (*w)[bhs::TC_W1 + bhs::tc_off(n, k, 16)] = h(p[bhs::OW1 + k * bhs::HID + n], 0.5f);
+    for (int k = 0; k < bhs::HID; ++k) {
+      (*w)[bhs::TC_W2 + bhs::tc_off(n, k, 64)] = h(p[bhs::OW2 + k * bhs::HID + n], 0.5f);
+      (*w)[bhs::TC_W3 + bhs::tc_off(n, k, 64)] = h(p[bhs::OW3 + k * bhs::HID + n], 0.5f);
+    }
+  }
+  for (int n = 0; n < bhs::NO; ++n)
+    for (int k = 0; k < bhs::HID; ++k)
+      (*w)[bhs::TC_W4 + bhs::tc_off(n, k, 64)] = h(p[bhs::OW4 + k * bhs::NO + n], 1.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,33 +392,10 @@ std::vector<float> init_params(uint64_t seed) {
   return p;
 }
 
-// B-operand fragments of the inference MLP from FP32 masters: the BF16
-// weights the network was trained with, held in FP16 (every BF16 value in
-// FP16's range is an FP16 value), those of the hidden layers and their
-// biases halved so the kernel's accumulators hold z / 2.
-void pack_fragments(const std::vector<float>& p, std::vector<uint2>* frag, std::vector<float>* bias) {
-  frag->assign(bhs::NFRAG, uint2{0u, 0u});
-  float scale = 0.5f;
-  auto bits = [&](float x) {
-    return (uint32_t)__half_as_ushort(__float2half_rn(scale * __bfloat162float(__float2bfloat16_rn(x))));
-  };
-  auto layer = [&](int off, int fr, int KB, int NJ, int ld) {
-    for (int kb = 0; kb < KB; ++kb)
-      for (int j = 0; j < NJ; ++j)
-        for (int l = 0; l < 32; ++l) {
-          const int g = l >> 2, t = l & 3, n = 8 * j + g;
-          auto W = [&](int k) { return p[off + k * ld + n]; };
-          uint2 v;
-          v.x = bits(W(16 * kb + 2 * t)) | (bits(W(16 * kb + 2 * t + 1)) << 16);
-          v.y = bits(W(16 * kb + 8 + 2 * t)) | (bits(W(16 * kb + 9 + 2 * t)) << 16);
-          (*frag)[fr + (kb * NJ + j) * 32 + l] = v;
-        }
-  };
-  layer(bhs::OW1, bhs::FR1, 1, 8, bhs::HID);
-  layer(bhs::OW2, bhs::FR2, 4, 8, bhs::HID);
-  layer(bhs::OW3, bhs::FR3, 4, 8, bhs::HID);
-  scale = 1.0f;
-  layer(bhs::OW4, bhs::FR4, 4, 1, bhs::NO);
+// Biases of the inference path: those of the hidden layers halved (the
+// tensor-core tiles hold the hidden layers' weights halved, so the
+// pre-activations come out as z / 2).
+void pack_bias(const std::vector<float>& p, std::vector<float>* bias) {
   bias->assign(bhs::NBIAS, 0.0f);
   for (int n = 0; n < bhs::HID; ++n) {
     (*bias)[n] = 0.5f * p[bhs::OB1 + n];
@@ -388,7 +404,6 @@ void pack_fragments(const std::vector<float>& p, std::vector<uint2>* frag, std::
   }
   for (int n = 0; n < 8; ++n) (*bias)[3 * bhs::HID + n] = p[bhs::OB4 + n];
 }
-
 
 // Flat-space exit angle alpha of the ray with impact parameter b at r.
 double alpha_of(double b, double r) { return M_PI - std::asin(std::min(1.0, b * std::sqrt(1.0 - 2.0 / r) / r)); }
@@ -466,18 +481,19 @@ struct Net {
 };
 
 int upload_surrogate(bh_scene* sc, SurrogateState* s) {
-  std::vector<uint2> frag;
   std::vector<float> bias;
-  pack_fragments(s->params, &frag, &bias);
+  pack_bias(s->params, &bias);
+  std::vector<uint16_t> wtc;
+  pack_tc_weights(s->params, &wtc);
   cudaError_t e = cudaSuccess;
-  if (!s->d_frag) e = cudaMalloc((void**)&s->d_frag, bhs::NFRAG * sizeof(uint2));
+  if (!s->d_w) e = cudaMalloc((void**)&s->d_w, bhs::TC_NW * sizeof(uint16_t));
   if (e == cudaSuccess && !s->d_bias) e = cudaMalloc((void**)&s->d_bias, bhs::NBIAS * sizeof(float));
   if (e == cudaSuccess) {
     if (s->d_table) cudaFree(s->d_table);
     s->d_table = nullptr;
     e = cudaMalloc((void**)&s->d_table, std::max<size_t>(1, s->table.size()));
   }
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_frag, frag.data(), bhs::NFRAG * sizeof(uint2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_w, wtc.data(), bhs::TC_NW * sizeof(uint16_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_bias, bias.data(), bhs::NBIAS * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_table, s->table.data(), s->table.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bh_cuda_fail(e, "surrogate upload");
@@ -493,26 +509,39 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
 
 // Run the inference kernel on host features (normalised), host outputs.
 int infer_host(const std::vector<float>& params, int n, const float* x, float* y, cudaStream_t st) {
-  std::vector<uint2> frag;
   std::vector<float> bias;
-  pack_fragments(params, &frag, &bias);
+  pack_bias(params, &bias);
+  std::vector<uint16_t> wtc;
+  pack_tc_weights(params, &wtc);
   DevBuf db;
-  uint2* d_frag;
+  uint16_t* d_w;
   float *d_bias, *d_x, *d_y;
-  cudaError_t e = db.alloc(&d_frag, bhs::NFRAG);
+  unsigned* d_status;
+  cudaError_t e = db.alloc(&d_w, bhs::TC_NW);
   if (e == cudaSuccess) e = db.alloc(&d_bias, bhs::NBIAS);
   if (e == cudaSuccess) e = db.alloc(&d_x, (size_t)bhs::K0 * n);
   if (e == cudaSuccess) e = db.alloc(&d_y, (size_t)3 * n);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_frag, frag.data(), bhs::NFRAG * sizeof(uint2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = db.alloc(&d_status, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, wtc.data(), bhs::TC_NW * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_bias, bias.data(), bhs::NBIAS * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_x, x, (size_t)bhs::K0 * n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(bhs::TcSmem));
   if (e != cudaSuccess) return bh_cuda_fail(e, "mlp inference setup");
-  const int blocks = std::max(1, std::min(1024, (n + 255) / 256));
-  k_mlp_infer<<<blocks, 256, 0, st>>>(n, d_x, d_frag, d_bias, d_y);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int groups = (n + 127) / 128;
+  const int blocks = std::max(1, std::min(groups, 2 * sms));
+  k_mlp_infer_tc<<<blocks, 128, sizeof(bhs::TcSmem), st>>>(n, d_x, d_w, d_bias, d_y, d_status);
   e = cudaGetLastError();
+  unsigned status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(y, d_y, (size_t)3 * n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return bh_cuda_fail(e, "mlp inference");
+  if (status) return bh_fail(BH_E_DEVICE, "mlp inference: a tensor-core layer did not complete");
   return BH_OK;
 }
 
@@ -930,10 +959,14 @@ extern "C" int bh_surrogate_load(bh_scene* sc, const char* path) {
 int surrogate_prepare(bh_scene* sc, const bh_camera* cams, int n_cams, const int* w, const int* h,
                       void* dirs, uint16_t* flags, uint32_t* rgba, const bh_render_opts* opts,
                       cudaStream_t upload_stream, CamK* cams_dev, PreparedRender* pr) {
-  if (!sc->surr || !sc->surr->d_frag)
+  if (!sc->surr || !sc->surr->d_w)
     return bh_fail(BH_E_NO_SURROGATE, "surrogate mode: no trained weights on this scene");
   if (sc->sk.ic != BH_IC_STATIC && sc->sk.ic != BH_IC_EUCLIDEAN)
     return bh_fail(BH_E_INVALID, "surrogate mode: unknown initial-condition convention");
+  {
+    const cudaError_t e = surrogate_kernel_setup();
+    if (e != cudaSuccess) return bh_cuda_fail(e, "surrogate mode: kernel set-up");
+  }
   const TunedShape t = tuned_shape(sc, BH_MODE_SURROGATE);
   bh_render_opts o = *opts;
   o.mode = BH_MODE_MIXED;
@@ -961,7 +994,7 @@ int surrogate_prepare(bh_scene* sc, const bh_camera* cams, int n_cams, const int
   pr->ls.join = sc->join;
   pr->ls.band_ev = sc->band_ev;
   pr->ls.band_warps = t.band_warps;
-  pr->p.mlp_frag = s->d_frag;
+  pr->p.mlp_w = s->d_w;
   pr->p.mlp_bias = s->d_bias;
   pr->p.surr_table = s->d_table;
   pr->p.surr_nb_lb = s->nb_lb;
@@ -996,7 +1029,7 @@ int surrogate_render(bh_scene* sc, const bh_camera* cams, int n_cams, const int*
 void surrogate_release(bh_scene* sc) {
   if (!sc->surr) return;
   SurrogateState* s = sc->surr;
-  cudaFree(s->d_frag);
+  cudaFree(s->d_w);
   cudaFree(s->d_bias);
   cudaFree(s->d_table);
   cudaFree(s->d_list);
