@@ -97,7 +97,9 @@ extern "C" {
 
 /* ---- device status bits (bh_stats.status) ----------------------------- */
 #define BH_STATUS_ABORTED 1u   /* abort_after item count reached            */
-#define BH_STATUS_WATCHDOG 2u  /* persistent loop iteration limit reached   */
+#define BH_STATUS_WATCHDOG 2u  /* persistent loop iteration limit reached, or
+                                  a tensor-core layer of the surrogate pass
+                                  not completed within its wait limit      */
 
 typedef struct bh_scene bh_scene; /* opaque; owns device state */
 

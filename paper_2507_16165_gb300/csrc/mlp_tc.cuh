@@ -28,7 +28,11 @@ constexpr int TC_W2 = TC_W1 + 64 * 16;  // 64 x 64
 constexpr int TC_W3 = TC_W2 + 64 * 64;  // 64 x 64
 constexpr int TC_W4 = TC_W3 + 64 * 64;  // 16 x 64
 constexpr int TC_NW = TC_W4 + 16 * 64;  // FP16 values
-constexpr int TC_COLS = 64;             // tensor-memory columns a CTA allocates
+// Tensor-memory columns a CTA allocates.  Every kernel that allocates tensor
+// memory (the surrogate pass, the inference kernel) holds about 54 KB of
+// shared memory a CTA, so at most four such CTAs share an SM: 256 of its
+// 512 columns, and an allocation never has to wait for another CTA's.
+constexpr int TC_COLS = 64;
 
 // FP16 element offset of (row, k) in a tile of K columns (K = 16 or 64).
 __host__ __device__ constexpr int tc_off(int row, int k, int K) {
