@@ -303,14 +303,17 @@ def test_network_gain_in_steps_and_time(trained):
           f"(x{t64 / tsu:.1f} over FP64, x{tmx / tsu:.2f} of mixed)")
 
 
-@pytest.mark.parametrize("spheres", [False, True])
-def test_surrogate_render_parity(trained, spheres):
+@pytest.mark.parametrize("size,spheres", [(256, False), (256, True), (70, False)])
+def test_surrogate_render_parity(trained, size, spheres):
+    """The surrogate render against the oracle.  The surrogate pass takes 128
+    queue slots a CTA; 70 x 70 leaves its queue (162 tiles of 8 x 4, 5184
+    slots) half a group short and its edge tiles part outside the image."""
     import torch
     w0, sc0 = trained
-    w = W.config4(256, spheres=spheres)
+    w = W.config4(size, spheres=spheres)
     sc = bh.Scene(w.scene)
     bh.bh_surrogate_load(sc.handle, WEIGHTS)
-    out = sc.render(w.cameras, "surrogate", rtol=1e-5, atol=1e-7)
+    out = sc.render(w.cameras, "surrogate", rtol=1e-5, atol=1e-7, tile_w=8, tile_h=4)
     torch.cuda.synchronize()
     bh.bh_scene_sync(sc.handle)
     st = sc.stats()
