@@ -125,8 +125,100 @@ def job_rate(rays_per_rank: int, steps: int, world: int, seconds: float) -> floa
     return world * rays_per_rank * steps / seconds / 1e6
 
 
+# The NVML poller, run as its own process so that it never competes with
+# the timed loop for the interpreter: it reads (never sets) the SM clock and
+# the clock-event reason bits of one GPU every millisecond and writes them to
+# a file, after printing "ready" once polling has begun.
+_NVML_POLLER = r"""
+import ctypes, signal, sys, time
+ident, out = sys.argv[1], sys.argv[2]
+lib = ctypes.CDLL("libnvidia-ml.so.1")
+if lib.nvmlInit_v2() != 0:
+    sys.exit(1)
+dev = ctypes.c_void_p()
+if ident.startswith("GPU-"):
+    ok = lib.nvmlDeviceGetHandleByUUID(ident.encode(), ctypes.byref(dev)) == 0
+else:
+    n = ctypes.c_uint()
+    lib.nvmlDeviceGetCount_v2(ctypes.byref(n))
+    ok = lib.nvmlDeviceGetHandleByIndex_v2(0 if n.value == 1 else int(ident), ctypes.byref(dev)) == 0
+if not ok:
+    sys.exit(1)
+reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+    lib.nvmlDeviceGetCurrentClocksThrottleReasons
+mx, clk, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx))
+stop = []
+signal.signal(signal.SIGTERM, lambda *a: stop.append(1))
+rows = []
+print("ready", flush=True)
+t_end = time.time() + 900
+while not stop and time.time() < t_end:
+    if lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0 and reasons(dev, ctypes.byref(rs)) == 0:
+        rows.append("%d %d %d" % (clk.value, mx.value, rs.value))
+    time.sleep(0.001)
+with open(out, "w") as f:
+    f.write("\n".join(rows))
+"""
+
+
+class NvmlPoller:
+    """SM clock and clock-event reasons of one GPU, read through NVML (the
+    driver's libnvidia-ml) every millisecond by a separate process; raises
+    OSError when NVML or the device cannot be found."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        import tempfile
+        ident = str(cuda_index)
+        try:
+            import torch
+            uuid = getattr(torch.cuda.get_device_properties(cuda_index), "uuid", None)
+            if uuid is not None:
+                ident = "GPU-" + str(uuid)
+        except Exception:
+            pass
+        fd, self.path = tempfile.mkstemp(prefix="bh_clocks_")
+        os.close(fd)
+        self.proc = subprocess.Popen([sys.executable, "-c", _NVML_POLLER, ident, self.path],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        # polling has begun once "ready" arrives (NVML found), else the process exits
+        line = self.proc.stdout.readline()
+        if line.strip() != "ready":
+            self.proc.wait(timeout=5)
+            os.unlink(self.path)
+            raise OSError("NVML poller unavailable")
+
+    def finish(self) -> dict | None:
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            return None
+        try:
+            with open(self.path) as f:
+                rows = [tuple(int(x) for x in ln.split()) for ln in f if ln.strip()]
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[0]) for r in rows)
+        bits = 0
+        for r in rows:
+            bits |= r[2]
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": sorted(n for b, n in self.REASONS.items() if bits & b),
+                "samples": len(sm), "source": "NVML every 1 ms (separate process)"}
+
+
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    """Clock and throttle-reason samples while the timed region runs: NVML
+    polled every millisecond by a separate process where the driver's library
+    loads (so that a region of a few tens of milliseconds holds many samples),
+    and nvidia-smi at 50 ms beside it (the summary's fallback)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,6 +229,8 @@ class ClockSampler:
         self.proc = None
         self.lines: list[str] = []
         self.thread = None
+        self.nvml = None
+        self.nvml_summary = None
 
     def __enter__(self):
         try:
@@ -148,6 +242,10 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+        try:
+            self.nvml = NvmlPoller(self.index)
+        except (OSError, subprocess.SubprocessError):
+            self.nvml = None
         return self
 
     def _read(self):
@@ -155,6 +253,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self.nvml:
+            self.nvml_summary = self.nvml.finish()
         if self.proc:
             self.proc.terminate()
             try:
@@ -165,6 +265,8 @@ class ClockSampler:
                 self.thread.join(timeout=2)
 
     def summary(self) -> dict:
+        if self.nvml_summary:
+            return self.nvml_summary
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for ln in self.lines:
@@ -183,7 +285,7 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi every 50 ms"}
 
 
 def cpu_baseline(w, seconds: float = 10.0, seed: int = 0) -> dict:
