@@ -408,6 +408,16 @@ int bh_mlp_grad(const float *params, int n, const float *x, const float *t, floa
  * not complete within the kernel's wait limit. */
 int bh_mlp_infer(const float *params, int n, const float *x, float *y, void *stream);
 
+/* Self-test of the bounded waits of the tensor-core kernels: one CTA
+ * allocates tensor memory as those kernels do, waits on an mbarrier that
+ * nothing arrives on with their wait (up to `tries` waits of `wait_ns`
+ * nanoseconds each, both clamped to [1, 10000] and [1, 1000000]), gives up,
+ * frees the tensor memory and reports.  *timed_out = 1 when the wait gave up
+ * (the expected outcome), *waited_ms = the wait's device time.  Nothing
+ * faults or hangs; the device stays usable.  Synchronous.  BH_E_INVALID for
+ * null outputs. */
+int bh_selftest_wait_timeout(int tries, int wait_ns, int *timed_out, double *waited_ms);
+
 /* ---- batched launch in a CUDA graph, autotuning ------------------------
  * One render of n_cams cameras (Sec. 3.2's scaling runs render many images;
  * here many cameras of uneven resolution share one persistent launch

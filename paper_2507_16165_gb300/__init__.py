@@ -28,7 +28,7 @@ __all__ = ["bh_version", "bh_last_error", "bh_scene_create", "bh_scene_destroy",
            "bh_render_stats", "bh_render_noalloc", "bh_graph_create", "bh_graph_launch",
            "bh_graph_destroy", "bh_autotune", "bh_autotune_reset", "bh_surrogate_labels",
            "bh_surrogate_train", "bh_surrogate_calibrate", "bh_surrogate_get", "bh_surrogate_save", "bh_surrogate_load",
-           "bh_mlp_grad", "bh_mlp_infer", "Scene", "render_opts",
+           "bh_mlp_grad", "bh_mlp_infer", "bh_selftest_wait_timeout", "Scene", "render_opts",
            "render_workload"]
 
 
@@ -299,6 +299,16 @@ def bh_mlp_grad(params, x, t, stream=None):
     check(_capi.lib().bh_mlp_grad(_ptr(params), n, _ptr(x), _ptr(t), _ptr(y), _ptr(g),
                                   ctypes.byref(loss), _stream_ptr(stream)), "bh_mlp_grad")
     return y, g, loss.value
+
+
+def bh_selftest_wait_timeout(tries: int = 20, wait_ns: int = 100000) -> dict:
+    """Run out the tensor-core kernels' bounded wait on purpose (nothing
+    arrives on its barrier): {"timed_out": bool, "waited_ms": float}."""
+    t = ctypes.c_int()
+    ms = ctypes.c_double()
+    check(_capi.lib().bh_selftest_wait_timeout(int(tries), int(wait_ns), ctypes.byref(t),
+                                               ctypes.byref(ms)), "bh_selftest_wait_timeout")
+    return {"timed_out": bool(t.value), "waited_ms": ms.value}
 
 
 def bh_mlp_infer(params, x, stream=None):

@@ -143,6 +143,7 @@ SIGNATURES = [
     ("bh_surrogate_load", _I, [_P, ctypes.c_char_p]),
     ("bh_mlp_grad", _I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     ("bh_mlp_infer", _I, [_P, _I, _P, _P, _P]),
+    ("bh_selftest_wait_timeout", _I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     ("bh_render_noalloc", _I, [ctypes.POINTER(bh_scene_desc), ctypes.POINTER(bh_camera), _I,
                                _P, _P, _P, _P, _P, ctypes.POINTER(bh_render_opts)]),
 ]

@@ -331,6 +331,32 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(int n, const float* __rest
   }
 }
 
+// The wait of the tensor-core kernels run out on purpose: tensor memory
+// allocated, an mbarrier that nothing arrives on, the same bounded wait,
+// then the same release of the tensor memory.  out[0] = 1 when the wait
+// gave up, out[1] = the clock64 cycles it took.
+__global__ void __launch_bounds__(32) k_tc_wait_probe(int tries, unsigned wait_ns,
+                                                      unsigned long long* out) {
+  __shared__ unsigned long long mbar;
+  __shared__ uint32_t taddr;
+  bhs::tmem_alloc(bhs::smem_u32(&taddr), bhs::TC_COLS);
+  if (threadIdx.x == 0) bhs::mbar_init(bhs::smem_u32(&mbar), 1);
+  bhs::tc_fence_before();
+  __syncwarp();
+  bhs::tc_fence_after();
+  if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    bool done = false;
+    for (int i = 0; i < tries && !done; ++i) done = bhs::mbar_wait(bhs::smem_u32(&mbar), 0u, wait_ns);
+    out[0] = done ? 0ull : 1ull;
+    out[1] = (unsigned long long)(clock64() - t0);
+  }
+  bhs::tc_fence_before();
+  __syncwarp();
+  bhs::tc_fence_after();
+  bhs::tmem_dealloc(taddr, bhs::TC_COLS);
+}
+
 // FP16 W^T tiles of the tensor-core path (the trained BF16 values, the
 // hidden layers' halved) from FP32 masters.
 void pack_tc_weights(const std::vector<float>& p, std::vector<uint16_t>* w) {
@@ -600,6 +626,28 @@ extern "C" int bh_mlp_grad(const float* params, int n, const float* x, const flo
   if (y)
     for (int i = 0; i < n; ++i)
       for (int k = 0; k < bhs::NOUT; ++k) y[3 * i + k] = z4[(size_t)i * bhs::NO + k];
+  return BH_OK;
+}
+
+extern "C" int bh_selftest_wait_timeout(int tries, int wait_ns, int* timed_out, double* waited_ms) {
+  if (!timed_out || !waited_ms) return bh_fail(BH_E_INVALID, "bh_selftest_wait_timeout: null output");
+  tries = std::min(10000, std::max(1, tries));
+  wait_ns = std::min(1000000, std::max(1, wait_ns));
+  DevBuf db;
+  unsigned long long* d_out;
+  cudaError_t e = db.alloc(&d_out, 2);
+  if (e == cudaSuccess) e = cudaMemset(d_out, 0, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_selftest_wait_timeout: setup");
+  k_tc_wait_probe<<<1, 32>>>(tries, (unsigned)wait_ns, d_out);
+  e = cudaGetLastError();
+  unsigned long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d_out, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bh_cuda_fail(e, "bh_selftest_wait_timeout");
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  *timed_out = (int)h[0];
+  *waited_ms = khz > 0 ? (double)h[1] / (double)khz : 0.0;
   return BH_OK;
 }
 

@@ -369,3 +369,23 @@ def test_surrogate_without_training_is_refused():
     finally:
         sc.close()
     torch.cuda.synchronize()
+
+
+def test_tensor_core_wait_gives_up_and_device_stays_usable():
+    """The tensor-core kernels' bounded wait, run out on purpose: one CTA
+    holds tensor memory and waits on a barrier that nothing arrives on.  The
+    wait gives up and reports, the tensor memory is released (a second run
+    allocates again), and the inference kernel, which allocates tensor
+    memory too, still runs and matches the FP64 network."""
+    for _ in range(2):
+        r = bh.bh_selftest_wait_timeout(tries=20, wait_ns=100000)
+        assert r["timed_out"]
+        assert 0.0 < r["waited_ms"] < 1000.0
+    rng = np.random.default_rng(3)
+    p = _rand_params(4)
+    x = np.zeros((256, 16), np.float32)
+    x[:, :mlp.NFEAT] = rng.uniform(-1, 1, (256, mlp.NFEAT))
+    y = bh.bh_mlp_infer(p, x)
+    y_r, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), use_bf16=True)
+    fwd, _ = _abs_bounds(p, x, np.zeros((256, 3)))
+    assert np.all(np.abs(y - y_r) <= INFER_ALLOW * fwd + 1e-6)
