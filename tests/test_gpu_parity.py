@@ -73,6 +73,63 @@ def test_pole_camera_and_zero_mass():
                       1e-10, 1e-10), "fp64")
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
+def test_inner_disk_and_near_spheres(mode):
+    """A disk reaching inside the photon sphere (r_in = 2.5M, so capture is
+    u >= 1/(2M) rather than the 1/(3M) early exit), spheres between 4M and
+    7M, and a close observer (r_obs = 18M): rays that wind near the photon
+    sphere, cross the disk inside it and meet spheres close to the hole."""
+    sc = W.Scene(mass=1.0, disk=(2.5, 15.0),
+                 spheres=W.seeded_spheres(5, n=4, r_range=(4.0, 7.0), radius_range=(0.3, 0.8)),
+                 sky_seed=2)
+    w = W.Workload("inner", sc, (W.Camera(18.0, 84.0, 96, 80, azim_deg=20.0),), mode,
+                   *_tol(mode))
+    _check(w, mode)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
+def test_distant_edge_on_observer(mode):
+    """r_obs = 200M looking exactly edge-on at the disk (inclination 90) with
+    a 12-degree field: u0 = 0.005, image-plane radii down to 1e-4 and a disk
+    seen in its own plane, where every ray's disk nodes sit at the ends of
+    its path.  The narrow field puts 8 of the 5184 pixels within 2e-3 M of
+    b_c.  There the pure FP32 form cannot hold 1e-4 rad: its FP32 state
+    (u, u') fixes b only to a few 2^-24 b, and the exit angle grows like
+    -ln(b - b_c), so its error is about 2^-24 b / |b - b_c| times the
+    roundings in the set-up (5.8e-4 rad measured at 1.6e-3 M, whatever the
+    step tolerances).  The FP32 case is held to the full bar on every pixel
+    outside 3e-3 M of b_c, to exact flags everywhere, and inside to
+    16 * 2^-24 b / |b - b_c|, the set-up's representation bound; FP64 and the
+    mixed form (FP64 turning point) to the full bar on every pixel."""
+    sc = W.Scene(mass=1.0, disk=(6.0, 30.0), sky_seed=4)
+    cam = W.Camera(200.0, 90.0, 72, 72, fov_deg=12.0)
+    w = W.Workload("far", sc, (cam,), mode, *_tol(mode))
+    if mode != "fp32":
+        _check(w, mode)
+        return
+    rtol, atol = _tol(mode)
+    got, st = render(w.scene, w.cameras, mode, rtol=rtol, atol=atol, band=w.band)
+    ref = oracle.render(w.scene, w.cameras, parity.oracle_opts(mode), nthreads=8)
+    assert parity.compare(got, ref, mode)["flag_mismatch"] == 0
+    n = cam.w * cam.h
+    ring = np.zeros(n, bool)
+    ring[parity.band_pixels(cam, 0.0, 3e-3)] = True
+    assert 0 < ring.sum() < 0.01 * n
+    pick = lambda d, idx: {k: np.asarray(v)[idx] for k, v in d.items()}
+    outside = np.flatnonzero(~ring)
+    parity.assert_parity(parity.compare(pick(got, outside), pick(ref, outside), mode), mode)
+    inside = np.flatnonzero(ring & ~np.isnan(ref["theta"]) & (ref["ambig"] == 0))
+    err = parity.great_circle(np.asarray(got["theta"])[inside], np.asarray(got["phi"])[inside],
+                              ref["theta"][inside], ref["phi"][inside])
+    s = np.tan(np.radians(cam.fov_deg) / 2.0)
+    x = (inside % cam.w + 0.5) * (2.0 * s / cam.w) - s
+    y = s - (inside // cam.w + 0.5) * (2.0 * s / cam.h)
+    rho2 = x * x + y * y
+    b = cam.r_obs * np.sqrt(rho2 / (1.0 + rho2)) / np.sqrt(1.0 - 2.0 / cam.r_obs)
+    bound = 16 * 2.0 ** -24 * b / np.abs(b - 3.0 * np.sqrt(3.0)) + 1e-4
+    assert np.all(err <= bound), (err.max(), bound.min())
+
+
 def test_euclidean_initial_conditions():
     """The paper's 'linear direction' reading of the initial conditions."""
     sc = replace(W.config2(64, "fp64").scene, ic=1)
