@@ -130,6 +130,20 @@ def test_distant_edge_on_observer(mode):
     assert np.all(err <= bound), (err.max(), bound.min())
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
+def test_close_observer(mode):
+    """An observer just outside the photon sphere (r_obs = 4.5M) with a
+    90-degree field, inside the disk's inner edge: steep initial slopes
+    (u'0 up to u0 cot(alpha) at alpha near 0), most inward rays captured,
+    the disk seen from within its hole, and spheres beyond it."""
+    sc = W.Scene(mass=1.0, disk=(6.0, 30.0),
+                 spheres=W.seeded_spheres(2, n=3, r_range=(8.0, 14.0), radius_range=(0.5, 1.5)),
+                 sky_seed=6)
+    w = W.Workload("close", sc, (W.Camera(4.5, 70.0, 80, 64, fov_deg=90.0, azim_deg=35.0),), mode,
+                   *_tol(mode))
+    _check(w, mode)
+
+
 def test_euclidean_initial_conditions():
     """The paper's 'linear direction' reading of the initial conditions."""
     sc = replace(W.config2(64, "fp64").scene, ic=1)
