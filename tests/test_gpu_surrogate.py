@@ -389,3 +389,27 @@ def test_tensor_core_wait_gives_up_and_device_stays_usable():
     y_r, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), use_bf16=True)
     fwd, _ = _abs_bounds(p, x, np.zeros((256, 3)))
     assert np.all(np.abs(y - y_r) <= INFER_ALLOW * fwd + 1e-6)
+
+
+@pytest.mark.parametrize("r_obs", [10.0, 150.0])
+def test_surrogate_outside_training_domain_falls_back(trained, r_obs):
+    """Observers outside the network's training domain (r_obs in [15, 100] M):
+    the network serves no ray, every ray goes to the integrator's fallback
+    passes, and the render matches the oracle at the surrogate form's bars."""
+    import torch
+    sc0 = W.config4(16, spheres=False).scene
+    cam = W.Camera(r_obs, 75.0, 64, 48, azim_deg=15.0, fov_deg=60.0 if r_obs < 50 else 12.0)
+    sc = bh.Scene(sc0)
+    bh.bh_surrogate_load(sc.handle, WEIGHTS)
+    out = sc.render([cam], "surrogate", rtol=1e-5, atol=1e-7)
+    torch.cuda.synchronize()
+    bh.bh_scene_sync(sc.handle)
+    st = sc.stats()
+    got = {"theta": out["theta"].double().cpu().numpy(), "phi": out["phi"].double().cpu().numpy(),
+           "flags": out["flags"].cpu().numpy().astype(np.uint16),
+           "rgba": out["rgba"].cpu().numpy().astype(np.uint32)}
+    sc.close()
+    assert st["n_surrogate"] == 0
+    assert st["n_fallback"] + st["n_band"] <= st["rays"] == cam.w * cam.h
+    ref = oracle.render(sc0, [cam], parity.oracle_opts("surrogate"), nthreads=8)
+    parity.assert_parity(parity.compare(got, ref, "surrogate"), "surrogate")
