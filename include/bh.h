@@ -314,7 +314,7 @@ int bh_render_stats(const bh_scene *scene, bh_stats *out);
  * error decides whether BH_MODE_SURROGATE may answer rays there.  Rays in
  * the photon-sphere band, outside the training domain, in a failing bin, or
  * whose orbital plane cuts a sphere are finished by the integrator.  There
- * is no surrogate in the paper; the integrator is the judge of its error. */
+ * is no surrogate in the paper; the integrator is the reference for its error. */
 typedef struct bh_train_opts {
   int epochs;            /* passes over the training samples (0: 20)       */
   int batch;             /* samples per Adam step, multiple of 32 (0: 16384) */
