@@ -458,7 +458,7 @@ __device__ bool step_events(const Params& p, Ray<R>& r, R& un, R& vn, R& fn, R& 
   for (int it = 0; it < 8 && r.phi_node <= pb; ++it) {
     const E uk = H.val_t(E((r.phi_node - pa) * R(H.ih)));
     if (uk > E(0)) {
-      const E rk = E(1) / uk;
+      const E rk = m_quot(E(1), uk);
       if (rk >= S.r_in && rk <= S.r_out) {
         consider<R, E>(EV_DISK, r.phi_node, 0u, bt, bp, bid);
         break;
@@ -897,9 +897,12 @@ __global__ void __maxnreg__(112) k_surrogate(const __grid_constant__ Params p) {
           serve = false;
         }
         if (serve) {
-          const float delta = fmaf(o[0], bhs::D_S, bhs::D_C) * 4.0f * M / b;
+          // the hardware reciprocal (a few ulp) throughout: far inside the
+          // form's 1e-3 rad bound and its 6e-2 M disk-edge ambiguity
+          const float ib = rcp_approx(b), iro = rcp_approx(r_obs);
+          const float delta = fmaf(o[0], bhs::D_S, bhs::D_C) * 4.0f * M * ib;
           const float alpha =
-              3.14159265358979f - asinf(fminf(1.0f, b * sqrtf(1.0f - 2.0f * M / r_obs) / r_obs));
+              3.14159265358979f - asinf(fminf(1.0f, b * sqrtf(1.0f - 2.0f * M * iro) * iro));
           const float phi_inf = alpha + delta;
           Hit<float> hit;
           hit.flags = BH_FLAG_ESC;
@@ -908,12 +911,13 @@ __global__ void __maxnreg__(112) k_surrogate(const __grid_constant__ Params p) {
           hit.v = 0.0f;
           if (p.s.disk_on) {
             const float pa = r.phi_node, pb = pa + 3.14159265358979f;
-            const float ua = o[1] / b, ub = o[2] / b;
-            if (pa < phi_inf && ua > 0.0f && 1.0f / ua >= S.r_in && 1.0f / ua <= S.r_out) {
+            const float ua = o[1] * ib, ub = o[2] * ib;
+            const float ra = rcp_approx(ua), rb = rcp_approx(ub);
+            if (pa < phi_inf && ua > 0.0f && ra >= S.r_in && ra <= S.r_out) {
               hit.flags = BH_FLAG_DISK;
               hit.phi = pa;
               hit.u = ua;
-            } else if (pb < phi_inf && ub > 0.0f && 1.0f / ub >= S.r_in && 1.0f / ub <= S.r_out) {
+            } else if (pb < phi_inf && ub > 0.0f && rb >= S.r_in && rb <= S.r_out) {
               hit.flags = BH_FLAG_DISK;
               hit.phi = pb;
               hit.u = ub;

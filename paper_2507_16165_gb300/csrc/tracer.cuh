@@ -105,6 +105,18 @@ __device__ __forceinline__ void pdl_wait_primary() {
 // in FP64.
 __device__ __forceinline__ float m_div(float a, float b) { return a * rcp_approx(b); }
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+// Quotient of the event location (interpolant scaling, root iterations,
+// sphere prefilter), which needs about 1e-14 relative in FP64, not a
+// correctly rounded result: the FP32 reciprocal refined by one FP64 Newton
+// step, y = y0 + y0 (1 - b y0) (relative error about 2^-46), three
+// operations on the FP64 pipe and two conversions instead of a division's
+// ten or so.  b = 0 or outside FP32's range gives NaN, which the root
+// search treats as a step outside its bracket.
+__device__ __forceinline__ float m_quot(float a, float b) { return a * rcp_approx(b); }
+__device__ __forceinline__ double m_quot(double a, double b) {
+  const double y0 = (double)rcp_approx((float)b);
+  return a * fma(y0, fma(-b, y0, 1.0), y0);
+}
 __device__ __forceinline__ float m_rsqrt(float x) { return rsqrt_approx(x); }
 __device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
 
@@ -327,7 +339,7 @@ struct Hermite {
   __device__ __forceinline__ void make(R pa_, R h_, R ua, R va, R fa, R ub, R vb, R fb) {
     pa = pa_;
     h = h_;
-    ih = m_div(R(1), h_);
+    ih = m_quot(R(1), h_);
     const R hh = h_ * h_;
     c0 = ua;
     c1 = h_ * va;
@@ -364,7 +376,7 @@ struct Hermite {
 template <typename R>
 __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
   R flo = H.val_t(lo) - target;
-  R t = lo + (hi - lo) * m_div(flo, flo - (H.val_t(hi) - target));
+  R t = lo + (hi - lo) * m_quot(flo, flo - (H.val_t(hi) - target));
   if (!(t > lo && t < hi)) t = R(0.5) * (lo + hi);
   for (int it = 0; it < Num<R>::root_iters; ++it) {
     const R f = H.val_t(t) - target;
@@ -376,7 +388,7 @@ __device__ R hermite_root(const Hermite<R>& H, R target, R lo, R hi) {
       hi = t;
     }
     const R df = H.dval_t(t);
-    R tn = t - m_div(f, df);
+    R tn = t - m_quot(f, df);
     if (m_abs(tn - t) * H.h < R(sizeof(R) == 8 ? 1e-15 : 1e-7)) return m_min(hi, m_max(lo, tn));
     if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
     t = tn;
@@ -625,15 +637,15 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<T>& r, int k, const Herm
     R sa, ca, sb, cb;
     m_sincos_evt(lo, &sa, &ca);
     m_sincos_evt(hi, &sb, &cb);
-    const R ia = m_div(R(1), ulo), ib = m_div(R(1), uhi);
+    const R ia = m_quot(R(1), ulo), ib = m_quot(R(1), uhi);
     const R ax = ca * ia, ay = sa * ia;
     const R bx = cb * ib - ax, by = sb * ib - ay;
     const R qx = cx - ax, qy = cy - ay;
     const R bb = m_fma(bx, bx, by * by);
-    R t = bb > R(0) ? m_div(m_fma(qx, bx, qy * by), bb) : R(0);
+    R t = bb > R(0) ? m_quot(m_fma(qx, bx, qy * by), bb) : R(0);
     t = m_min(R(1), m_max(R(0), t));
     const R dx = qx - t * bx, dy = qy - t * by;
-    const R q = m_div(m_max(ulo, uhi), m_min(ulo, uhi));
+    const R q = m_quot(m_max(ulo, uhi), m_min(ulo, uhi));
     const R hh = hi - lo;
     const R margin = R(0.47) * S.M3 * q * q * hh * hh + R(1e-6);
     const R reach = m_sqrt(rp2) + margin;
@@ -883,7 +895,7 @@ __device__ void finish_ray(const Params& p, const Ray<R>& r, const Hit<R>& hit,
     else
       sky_rgb<T>(s, th, ph, c);
   } else if (fl == BH_FLAG_DISK) {
-    const float rr = (float)(R(1) / hit.u);
+    const float rr = (float)m_quot(R(1), hit.u);
     float t = ex2_approx(0.75f * lg2_approx(s.f.r_in * rcp_approx(rr)));
     float bright = 1.0f;
     if (p.doppler) {
