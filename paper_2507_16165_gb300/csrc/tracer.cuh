@@ -657,13 +657,14 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<T>& r, int k, const Herm
     *phi_hit = lo;
     return true;
   }
-  R a_lo = lo, a_hi;
+  R a_lo = lo, a_hi, g_lo = glo, g_hi;
   const R ghi = sphere_g(cx, cy, K, hi, uhi);
   if (ghi <= R(0)) {
     a_hi = hi;
+    g_hi = ghi;
   } else {
     // golden-section search for the minimum of g on [lo, hi]
-    R x0 = lo, x3 = hi;
+    R x0 = lo, x3 = hi, g0 = glo;
     const R gr = R(0.6180339887498949);
     R x1 = x3 - gr * (x3 - x0), x2 = x0 + gr * (x3 - x0);
     R g1 = sphere_g(cx, cy, K, x1, H.u_at(x1));
@@ -682,6 +683,7 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<T>& r, int k, const Herm
         g1 = sphere_g(cx, cy, K, x1, H.u_at(x1));
       } else {
         x0 = x1;
+        g0 = g1;
         x1 = x2;
         g1 = g2;
         x2 = x0 + gr * (x3 - x0);
@@ -691,16 +693,32 @@ __device__ bool sphere_entry(const SceneK& s, const Ray<T>& r, int k, const Herm
     }
     if (!found) return false;
     a_hi = (g1 <= R(0)) ? x1 : x2;
+    g_hi = (g1 <= R(0)) ? g1 : g2;
     a_lo = x0;
+    g_lo = g0;
   }
-  // bisection on the entry: g(a_lo) > 0 >= g(a_hi)
+  // the entry: g(a_lo) > 0 >= g(a_hi), by regula falsi with the Illinois
+  // modification (the value kept at an end that stays twice is halved), so
+  // the bracket shrinks from both sides; a point outside the open bracket
+  // falls back to the midpoint.  The bracket holds the entry throughout, as
+  // bisection's does, and converges superlinearly instead of linearly.
+  int side = 0;
   for (int it = 0; it < Num<R>::root_iters; ++it) {
-    const R mid = R(0.5) * (a_lo + a_hi);
+    R mid = a_lo + (a_hi - a_lo) * m_quot(g_lo, g_lo - g_hi);
+    if (!(mid > a_lo && mid < a_hi)) mid = R(0.5) * (a_lo + a_hi);
     if (!(mid > a_lo && mid < a_hi)) break;
-    if (sphere_g(cx, cy, K, mid, H.u_at(mid)) > R(0))
+    const R gm = sphere_g(cx, cy, K, mid, H.u_at(mid));
+    if (gm > R(0)) {
       a_lo = mid;
-    else
+      g_lo = gm;
+      if (side == 1) g_hi *= R(0.5);
+      side = 1;
+    } else {
       a_hi = mid;
+      g_hi = gm;
+      if (side == -1) g_lo *= R(0.5);
+      side = -1;
+    }
     if (a_hi - a_lo < R(sizeof(R) == 8 ? 1e-14 : 1e-7)) break;
   }
   *phi_hit = a_hi;
