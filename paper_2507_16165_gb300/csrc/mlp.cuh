@@ -120,15 +120,4 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t* hi, uin
   *lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Split of an FP32 pair into FP16 high and low parts (x = hi + lo to about
-// 2^-22 relative), the inputs and activations of the inference path
-// (mlp_tc.cuh).
-__device__ __forceinline__ void split_pack_h(float x0, float x1, uint32_t* hi, uint32_t* lo) {
-  const __half2 h = __floats2half2_rn(x0, x1);
-  const float2 hf = __half22float2(h);
-  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-  *hi = *reinterpret_cast<const uint32_t*>(&h);
-  *lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 }  // namespace bhs

@@ -2,11 +2,14 @@
 // threads evaluates the network for 128 rows at a time (row r = thread r).
 // Each layer is D[128 x N] = A[128 x K] B[K x N] by tcgen05.mma (kind::f16,
 // FP16 operands, FP32 accumulation in tensor memory), issued by one thread;
-// A (the inputs, or the previous layer's activations as FP16 high + low
-// parts: two MMAs per K block) and B (the layer's weights, W^T) are read from
-// shared memory through matrix descriptors.  Warp w reads rows 32w..32w+31
-// of D from tensor memory lanes 32w..32w+31 (tcgen05.ld), adds the bias,
-// applies the SiLU and writes the next layer's A back to shared memory.
+// A (the inputs, or the previous layer's activations as FP16 high parts
+// and negated low parts: two MMAs per K block, the second with A negated)
+// and B (the layer's weights, W^T) are read from shared memory through
+// matrix descriptors, and D starts from the layer's bias, which each thread
+// writes into its own tensor-memory lane (tcgen05.st) beforehand.  Warp w
+// reads rows 32w..32w+31 of D from tensor memory lanes 32w..32w+31
+// (tcgen05.ld), applies the SiLU and writes the next layer's A back to
+// shared memory.
 //
 // Shared-memory tiles use the canonical K-major layout without swizzling:
 // 8 x 8 core matrices of 8 rows of 16 bytes (8 FP16 values along K), the
@@ -64,6 +67,8 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Negate-A bit of the instruction descriptor (bit 13): D += -A B.
+constexpr uint32_t TC_NEG_A = 1u << 13;
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -135,13 +140,77 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Eight FP32 values as FP16 high and low parts, packed for one 16-byte store each.
-__device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* lo) {
+// An FP32 pair as FP16 high parts hi = fp16(x) and negated low parts
+// nlo = fp16(hi - x): hi - x is exact in FP32, and with the hi operand
+// added and the nlo operand subtracted (the MMA's negate-A bit) the two
+// MMAs of a K block sum to x to about 2^-22 relative.  The difference is
+// one mixed-precision subtract per value (FP16 minuend, FP32 subtrahend).
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t* hi, uint32_t* nlo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h);
+  float d0, d1;
+  asm("{\n\t.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\t"
+      "sub.rn.f32.f16 %0, a, %3;\n\tsub.rn.f32.f16 %1, b, %4;\n\t}\n"
+      : "=f"(d0), "=f"(d1)
+      : "r"(hb), "f"(x0), "f"(x1));
+  const __half2 l = __floats2half2_rn(d0, d1);
+  *hi = hb;
+  *nlo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Eight FP32 values as high and negated low parts, packed for one 16-byte
+// store each.
+__device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* nlo) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) split_pack_h(x[2 * q], x[2 * q + 1], &h[q], &l[q]);
+  for (int q = 0; q < 4; ++q) split_pair(x[2 * q], x[2 * q + 1], &h[q], &l[q]);
   *hi = make_uint4(h[0], h[1], h[2], h[3]);
-  *lo = make_uint4(l[0], l[1], l[2], l[3]);
+  *nlo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// 16 consecutive 32-bit columns of this thread's tensor-memory lane set to
+// v (completion is waited for with tmem_st_wait).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+      "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// A layer's bias, columns 16c..16c+15, into this thread's accumulator lane
+// (the layer's MMAs then accumulate onto it).  The output layer has 8
+// stored bias values; its columns 8..15 are not read.
+__device__ __forceinline__ void bias_to_tmem(const TcSmem& s, uint32_t lane_addr, int layer, int c) {
+  float b[16];
+  if (layer < 3) {
+    const float4* src = reinterpret_cast<const float4*>(s.bias + HID * layer + 16 * c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = src[q];
+      b[4 * q] = t.x;
+      b[4 * q + 1] = t.y;
+      b[4 * q + 2] = t.z;
+      b[4 * q + 3] = t.w;
+    }
+  } else {
+    const float4* src = reinterpret_cast<const float4*>(s.bias + 3 * HID);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float4 t = src[q];
+      b[4 * q] = t.x;
+      b[4 * q + 1] = t.y;
+      b[4 * q + 2] = t.z;
+      b[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int j = 8; j < 16; ++j) b[j] = 0.0f;
+  }
+  tmem_st16(lane_addr + 16u * c, b);
 }
 
 // Waits of up to kTcWaitNs each allowed on a layer's completion before the
@@ -169,6 +238,9 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
     *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 8, 16)]) = hi;
     *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 8, 16)]) = lo;
   }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) bias_to_tmem(s, lane_addr, 0, c);
+  tmem_st_wait();
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -178,9 +250,10 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
     if (r == 0) {
       tc_fence_after();
       const uint32_t ahi = smem_u32(s.a_hi), alo = smem_u32(s.a_lo);
+      // accumulating onto the bias; the low parts subtracted
       if (L == 0) {
         const uint64_t b = tc_desc(smem_u32(s.w + TC_W1), 128, 256);
-        tc_mma(tmem, tc_desc(alo, 128, 256), b, tc_idesc(128, 64), 0u);
+        tc_mma(tmem, tc_desc(alo, 128, 256), b, tc_idesc(128, 64) | TC_NEG_A, 1u);
         tc_mma(tmem, tc_desc(ahi, 128, 256), b, tc_idesc(128, 64), 1u);
       } else {
         const int wo = L == 1 ? TC_W2 : (L == 2 ? TC_W3 : TC_W4);
@@ -189,7 +262,7 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
           const uint64_t b = tc_desc(wb + 256u * kb, 128, 1024);
-          tc_mma(tmem, tc_desc(alo + 256u * kb, 128, 1024), b, id, kb > 0 ? 1u : 0u);
+          tc_mma(tmem, tc_desc(alo + 256u * kb, 128, 1024), b, id | TC_NEG_A, 1u);
           tc_mma(tmem, tc_desc(ahi + 256u * kb, 128, 1024), b, id, 1u);
         }
       }
@@ -205,16 +278,14 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
     if (__syncthreads_or(!done)) ok = false;
     tc_fence_after();
     if (L < 3) {
-      const float* bias = s.bias + HID * L;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float v[16];
         tmem_ld16(lane_addr + 16u * c, v);
+        // the next layer's bias into the columns just read
+        if (L < 2 || c == 0) bias_to_tmem(s, lane_addr, L + 1, c);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float h = v[j] + bias[16 * c + j];
-          v[j] = fmaf(h, tanh_approx(h), h);
-        }
+        for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], tanh_approx(v[j]), v[j]);
         uint4 hi, lo;
         split8(v, &hi, &lo);
         *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 16 * c, 64)]) = hi;
@@ -223,16 +294,16 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
         *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 16 * c + 8, 64)]) = hi;
         *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 16 * c + 8, 64)]) = lo;
       }
+      tmem_st_wait();
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
     } else {
       float v[16];
       tmem_ld16(lane_addr, v);
-      const float* b4 = s.bias + 3 * HID;
-      o[0] = v[0] + b4[0];
-      o[1] = v[1] + b4[1];
-      o[2] = v[2] + b4[2];
+      o[0] = v[0];
+      o[1] = v[1];
+      o[2] = v[2];
       tc_fence_before();
     }
   }
