@@ -35,7 +35,6 @@ TunedShape default_shape(int mode) {
     t.block = 128;
     t.blocks_per_sm = 8;
   }
-  t.band_lanes = 32;
   t.band_warps = 4;
   return t;
 }

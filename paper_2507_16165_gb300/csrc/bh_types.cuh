@@ -221,7 +221,7 @@ struct Params {
   WorkK* ws;
   void* spill;        // Spill<R>[n_queue]
   int* band_list;     // queue slots deferred to FP64 [n_queue]
-  int band_lanes;       // lanes of a band-pass warp that take rays (1..32)
+  int band_trim;      // MIXED: band-pass warps beyond the list's need leave at once
   // surrogate mode
   const uint16_t* mlp_w;       // FP16 W^T tiles of the tensor-core path (bhs::TC_NW)
   const float* mlp_bias;       // bhs::NBIAS

@@ -372,7 +372,6 @@ RenderConfig resolve_config(const bh_scene* sc, const bh_render_opts* o) {
   c.budget = o->budget ? o->budget : t.budget;
   c.chunk = o->queue_chunk ? o->queue_chunk : t.chunk;
   if (c.spp_n > 1) c.budget = c.max_steps;  // every sample finishes in the tile pass
-  c.band_lanes = t.band_lanes;
   c.band_warps = t.band_warps;
   c.peri_reset = o->periastron_reset < 0 ? 0 : (o->periastron_reset == 2 ? 2 : 1);
   c.abort_after = o->abort_after;
@@ -465,6 +464,7 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   }
   p.cams = sc->d_cams;
   p.n_cams = n_cams;
+  p.band_trim = cfg.mode == BH_MODE_MIXED ? 1 : 0;
   p.tile_w = cfg.tile_w;
   p.tile_h = cfg.tile_h;
   p.tile_shift = ilog2(cfg.tile_w * cfg.tile_h);
@@ -495,7 +495,6 @@ void fill_params(const bh_scene* sc, const RenderConfig& cfg, int n_cams, long l
   p.ws = sc->d_ws;
   p.spill = sc->d_spill;
   p.band_list = sc->d_band;
-  p.band_lanes = cfg.band_lanes;
   fill_tolerances(p);
 }
 

@@ -246,7 +246,6 @@ extern "C" int bh_render_noalloc(const bh_scene_desc* desc, const bh_camera* cam
   p.ws = ws;
   p.spill = nullptr;
   p.band_list = nullptr;
-  p.band_lanes = 32;
   fill_tolerances(p);
   LaunchShape ls{num_sms, opts->block_size ? opts->block_size : 256, opts->blocks_per_sm};
   e = launch_coherent_only(p, f64 ? MODE_FP64 : MODE_FP32, ls, stream);

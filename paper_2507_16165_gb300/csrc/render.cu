@@ -693,8 +693,7 @@ __device__ __forceinline__ void list_pass(const Params& p, LocalStats& st) {
   bool active = false, exhausted = false;
   for (long long guard = 0; guard < (1ll << 40); ++guard) {
     if (!exhausted) {
-      const int lanes = SRC == SRC_BAND ? p.band_lanes : 32;
-      const unsigned need = __ballot_sync(kFull, !active && lane < lanes);
+      const unsigned need = __ballot_sync(kFull, !active);
       if (need) {
         unsigned long long base = 0;
         if (lane == 0) {
@@ -734,7 +733,15 @@ __device__ __forceinline__ void list_pass(const Params& p, LocalStats& st) {
 
 // The FP64 band pass is held to 64 registers, so one band warp and seven
 // 128-thread FP32 blocks fill an SM sub-partition's register file; it lets
-// the dependent coherent pass launch at once (see k_coherent).
+// the dependent coherent pass launch at once (see k_coherent).  Of its
+// one-warp blocks (band_warps per SM), only as many stay as the band list
+// needs for about 1.7 rays a lane, and never fewer than half: the others
+// leave at once and give their registers to the coherent pass beside it
+// (MIXED only).  At 4096^2 (config 3: 16,172 band rays) two warps per SM
+// (1.66 rays a lane) made the mixed frame 0.712 -> 0.700 ms; one (3.3 rays
+// a lane) made the band pass the frame's tail (0.96 ms).  Beside the
+// surrogate pass, whose shared memory fixes its residency, the band pass
+// keeps all its warps (two per SM measured 0.4% slower there).
 // The long-ray pass over spilled rays is launched as the programmatic
 // dependent of the pass that spills them, so its blocks are scheduled while
 // that pass drains; it waits for the pass to complete (and its spill list
@@ -746,6 +753,13 @@ __global__ void __launch_bounds__(512, MODE == MODE_BAND64 ? 2 : kMinBlocks<R>)
   // the pass that fills the list may still run (a programmatic launch):
   // wait for it to complete and its writes to be visible
   pdl_wait_primary();
+  if (SRC == SRC_BAND && p.band_trim) {
+    const unsigned long long n = *(volatile unsigned long long*)&p.ws->band_count;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long want = (n * 10ull + 32ull * 17ull - 1ull) / (32ull * 17ull);
+    const unsigned long long keep = want < warps / 2 ? warps / 2 : (want < warps ? want : warps);
+    if ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) >= keep) return;
+  }
   LocalStats st;
   st.zero();
   list_pass<R, MODE, OutR, SRC>(p, st);

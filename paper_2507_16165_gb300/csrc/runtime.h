@@ -55,7 +55,7 @@ struct RenderConfig {
   int doppler;
   int max_steps;
   int block, blocks_per_sm, tile_w, tile_h, budget, chunk;
-  int band_lanes, band_warps;
+  int band_warps;
   int peri_reset;
   unsigned long long abort_after;
 };
@@ -64,7 +64,7 @@ struct RenderConfig {
 struct TunedShape {
   int block, blocks_per_sm, tile_w, tile_h, budget;
   int chunk;  // queue slots per warp grab
-  int band_lanes, band_warps;  // MIXED FP64 band pass: lanes per warp, warps per SM
+  int band_warps;  // FP64 band pass: warps per SM launched (see k_longrays)
 };
 
 class DeviceGuard {

@@ -1042,6 +1042,7 @@ int surrogate_prepare(bh_scene* sc, const bh_camera* cams, int n_cams, const int
   pr->ls.join = sc->join;
   pr->ls.band_ev = sc->band_ev;
   pr->ls.band_warps = t.band_warps;
+  pr->p.band_trim = 0;  // the band pass keeps its warps beside the surrogate pass
   pr->p.mlp_w = s->d_w;
   pr->p.mlp_bias = s->d_bias;
   pr->p.surr_table = s->d_table;
