@@ -238,8 +238,11 @@ __device__ __forceinline__ long long pixel_slot(const Params& p, const CamK& c, 
 // (radial) or deferred to the FP64 band list.
 // WCULL: the 32 lanes of the warp call it together for a group of 32 slots
 // (one camera) and share one sphere cull (warp_sphere_candidates); else each
-// ray tests every sphere.
-template <typename R, int MODE, typename OutR, bool SPP = false, bool WCULL = false>
+// ray tests every sphere.  SURR: the surrogate pass's set-up, which needs the
+// plane, b, the first disk node and whether a sphere is cut, and none of the
+// integrator's state (sphere windows, turning point, tolerance tier).
+template <typename R, int MODE, typename OutR, bool SPP = false, bool WCULL = false,
+          bool SURR = false>
 __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& st, R* b_out,
                            R ox = R(0.5), R oy = R(0.5), SppAcc* acc = nullptr) {
   int cam, px, py, out;
@@ -258,13 +261,14 @@ __device__ bool setup_slot(const Params& p, long long q, Ray<R>& r, LocalStats& 
   r.aux = (MODE == MODE_FP64 || MODE == MODE_BAND64) ? BH_FLAG_FP64 : 0u;
   if (MODE == MODE_BAND64) r.aux |= BH_FLAG_BAND;
   R b, cos_a;
-  if (plane_setup<R>(p.s, c, sx, sy, cand, r, &b, &cos_a)) {
+  if (plane_setup<R, !SURR>(p.s, c, sx, sy, cand, r, &b, &cos_a)) {
     R P[3], d[3];
     camera_ray<R>(c, px, py, P, d, ox, oy);
     st.count_flag(radial_ray<R, OutR, SPP>(p, P, d, cos_a, out, r.aux, acc));
     return false;
   }
   *b_out = b;
+  if (SURR) return true;
   const TolR<R>& tol = TolPick<R, MODE>::get(p);
   const bool d64 = (MODE == MODE_FP64 || MODE == MODE_BAND64);
   // rays at least kFarB from the critical impact parameter, whose exit
@@ -908,7 +912,7 @@ __global__ void __maxnreg__(112) k_surrogate(const __grid_constant__ Params p) {
       SphWin win;
       r.win = &win;
       float b = 0.0f;
-      bool active = setup_slot<float, MODE_MIXED, float, false, true>(p, q, r, st, &b);
+      bool active = setup_slot<float, MODE_MIXED, float, false, true, true>(p, q, r, st, &b);
       bool serve = false;
       float r_obs = 0.0f;
       float f[bhs::K0];

@@ -531,8 +531,11 @@ __device__ __forceinline__ unsigned warp_sphere_candidates(const SceneK& s, cons
 // Orbital-plane set-up of the ray through image-plane point (sx, sy) of
 // camera cam.  Returns 0 for a ray to integrate, 1 for a radial ray (handled
 // by the caller with straight-line geometry).  cand: the spheres to test
-// for a cut of the plane (warp_sphere_candidates, or all of them).
-template <typename R>
+// for a cut of the plane (warp_sphere_candidates, or all of them).  WIN:
+// the angular windows of the cut spheres too; without them (the surrogate
+// pass, which hands every ray whose plane cuts a sphere to the integrator)
+// sph_mask holds the first cut sphere only.
+template <typename R, bool WIN = true>
 __device__ int plane_setup(const SceneK& s, const CamK& cam, R sx, R sy, unsigned cand, Ray<R>& r,
                            R* b_out, R* cos_a_out) {
   const CamR<R>& C = CR<R>(cam);
@@ -590,11 +593,12 @@ __device__ int plane_setup(const SceneK& s, const CamK& cam, R sx, R sy, unsigne
     const R nc = m_fma(sx, C.uc[k], -sy * C.rc[k]);
     if (m_abs(nc) < S.rad[k] * rho2 * irho && b <= S.cull_b[k]) {
       mask |= 1u << k;
+      if (!WIN) break;
       sphere_window_setup(s, r, k, (float)C.ec[k], (float)(m_fma(sx, C.rc[k], sy * C.uc[k]) * irho));
     }
   }
   r.sph_mask = mask;
-  if (mask) r.phi_sph = next_sphere_window(r, R(0));
+  if (WIN && mask) r.phi_sph = next_sphere_window(r, R(0));
   return 0;
 }
 
