@@ -11,6 +11,7 @@ the 99.9th-percentile and RGBA bars are those of the whole frame, with no
 pixel left out; flags are bit-exact on every sampled pixel outside the
 oracle's ambiguity mask."""
 import os
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -33,6 +34,9 @@ FULL = {
     "c3_mixed_4096": (W.config3(4096, "mixed"), "mixed", {}),
     # the mixed form with the FP64 turning-point solve for every ray
     "c3_mixed_literal_4096": (W.config3(4096, "mixed"), "mixed", {"periastron_reset": 2}),
+    # twice the FP64 band: more band rays than two band warps per SM take at
+    # about 1.7 a lane, so the band pass keeps more of its warps
+    "c3_mixed_wide_band_4096": (replace(W.config3(4096, "mixed"), band=0.1), "mixed", {}),
     "c4_surrogate_4096": (W.config4(4096), "surrogate", {}),
 }
 
@@ -98,6 +102,9 @@ def test_full_size_sampled_parity(name):
         parity.assert_parity(m, mode)
         if mode == "mixed":
             assert st["n_band"] > 0 and np.any(got["flags"] & bh.BH_FLAG_BAND)
+        if name == "c3_mixed_wide_band_4096":
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            assert st["n_band"] > 2 * sms * 32 * 1.7, st["n_band"]
         if mode == "surrogate":
             assert st["n_surrogate"] > 0.3 * n
     finally:
