@@ -1,21 +1,21 @@
 // The surrogate MLP on the fifth-generation tensor cores: one CTA of 128
 // threads evaluates the network for 128 rows at a time (row r = thread r).
 // Each layer is D[128 x N] = A[128 x K] B[K x N] by tcgen05.mma (kind::f16,
-// FP16 operands, FP32 accumulation in tensor memory), issued by one thread;
-// A (the inputs, or the previous layer's activations as FP16 high parts
-// and negated low parts: two MMAs per K block, the second with A negated)
-// and B (the layer's weights, W^T) are read from shared memory through
-// matrix descriptors, and D starts from the layer's bias, which each thread
-// writes into its own tensor-memory lane (tcgen05.st) beforehand.  Warp w
-// reads rows 32w..32w+31 of D from tensor memory lanes 32w..32w+31
-// (tcgen05.ld), applies the SiLU and writes the next layer's A back to
-// shared memory.
+// FP16 operands, FP32 accumulation in tensor memory), issued by one thread.
+// A (the inputs, or the previous layer's activations as FP16 high parts and
+// negated low parts: two MMAs per K block, the second with A negated) is
+// read from tensor memory, row m in lane m; B (the layer's weights, W^T)
+// from shared memory through matrix descriptors; D starts from the layer's
+// bias.  Warp w reads rows 32w..32w+31 of D from tensor memory lanes
+// 32w..32w+31 (tcgen05.ld), applies the SiLU and writes the next layer's A
+// and bias into the same lanes (tcgen05.st): the activations never leave
+// tensor memory and registers.
 //
-// Shared-memory tiles use the canonical K-major layout without swizzling:
-// 8 x 8 core matrices of 8 rows of 16 bytes (8 FP16 values along K), the
-// core matrices adjacent along K 128 bytes apart (the leading-dimension
-// byte offset) and the groups of 8 rows K/8 * 128 bytes apart (the stride
-// byte offset).
+// The weight tiles in shared memory use the canonical K-major layout
+// without swizzling: 8 x 8 core matrices of 8 rows of 16 bytes (8 FP16
+// values along K), the core matrices adjacent along K 128 bytes apart (the
+// leading-dimension byte offset) and the groups of 8 rows K/8 * 128 bytes
+// apart (the stride byte offset).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -31,11 +31,14 @@ constexpr int TC_W2 = TC_W1 + 64 * 16;  // 64 x 64
 constexpr int TC_W3 = TC_W2 + 64 * 64;  // 64 x 64
 constexpr int TC_W4 = TC_W3 + 64 * 64;  // 16 x 64
 constexpr int TC_NW = TC_W4 + 16 * 64;  // FP16 values
-// Tensor-memory columns a CTA allocates.  Every kernel that allocates tensor
-// memory (the surrogate pass, the inference kernel) holds about 54 KB of
-// shared memory a CTA, so at most four such CTAs share an SM: 256 of its
+// Tensor-memory columns a CTA allocates: the accumulators (columns 0-63,
+// FP32) and the layer inputs as packed FP16 pairs, high parts (64-95) and
+// negated low parts (96-127).  Every kernel that allocates tensor memory
+// (the surrogate pass, the inference kernel) holds about 54 KB of shared
+// memory a CTA (TcSmem::reserve), so at most four such CTAs share an SM: its
 // 512 columns, and an allocation never has to wait for another CTA's.
-constexpr int TC_COLS = 64;
+constexpr int TC_COLS = 128;
+constexpr uint32_t TC_A_HI = 64, TC_A_LO = 96;
 
 // FP16 element offset of (row, k) in a tile of K columns (K = 16 or 64).
 __host__ __device__ constexpr int tc_off(int row, int k, int K) {
@@ -44,8 +47,7 @@ __host__ __device__ constexpr int tc_off(int row, int k, int K) {
 
 struct TcSmem {
   uint16_t w[TC_NW];        // weights (the hidden layers' halved)
-  uint16_t a_hi[128 * 64];  // layer inputs, high FP16 parts
-  uint16_t a_lo[128 * 64];  // low parts
+  unsigned char reserve[32768];  // unused: keeps four CTAs an SM (see TC_COLS)
   float bias[NBIAS];        // b1 / 2, b2 / 2, b3 / 2, first 8 of b4
   unsigned long long mbar;  // completion of the layer's MMAs
   uint32_t tmem;            // tensor-memory base address
@@ -70,12 +72,15 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
 // Negate-A bit of the instruction descriptor (bit 13): D += -A B.
 constexpr uint32_t TC_NEG_A = 1u << 13;
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t accumulate) {
+// D (+)= A B with A read from tensor memory (a_tmem: lane 0, first column of
+// the K block; row m of A in lane m, two FP16 values a column) and B from a
+// shared-memory descriptor.
+__device__ __forceinline__ void tc_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -158,16 +163,6 @@ __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t* hi, uin
   *nlo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Eight FP32 values as high and negated low parts, packed for one 16-byte
-// store each.
-__device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* nlo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) split_pair(x[2 * q], x[2 * q + 1], &h[q], &l[q]);
-  *hi = make_uint4(h[0], h[1], h[2], h[3]);
-  *nlo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 // 16 consecutive 32-bit columns of this thread's tensor-memory lane set to
 // v (completion is waited for with tmem_st_wait).
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
@@ -180,6 +175,24 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
 }
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Eight consecutive 32-bit columns of this thread's tensor-memory lane set
+// to u (completion is waited for with tmem_st_wait).
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t* u) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+               "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7])
+               : "memory");
+}
+
+// Sixteen FP32 values as the high and negated low FP16 parts of eight
+// packed columns of A, written to this thread's lane at column col.
+__device__ __forceinline__ void a_to_tmem(uint32_t lane_addr, uint32_t col, const float* x) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) split_pair(x[2 * q], x[2 * q + 1], &h[q], &l[q]);
+  tmem_st8u(lane_addr + TC_A_HI + col, h);
+  tmem_st8u(lane_addr + TC_A_LO + col, l);
 }
 
 // A layer's bias, columns 16c..16c+15, into this thread's accumulator lane
@@ -229,18 +242,11 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
   const int w = r >> 5;
   const uint32_t mbar = smem_u32(&s.mbar);
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * w) << 16);
-  {
-    uint4 hi, lo;
-    split8(f, &hi, &lo);
-    *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 0, 16)]) = hi;
-    *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 0, 16)]) = lo;
-    split8(f + 8, &hi, &lo);
-    *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 8, 16)]) = hi;
-    *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 8, 16)]) = lo;
-  }
+  a_to_tmem(lane_addr, 0, f);
 #pragma unroll
   for (int c = 0; c < 4; ++c) bias_to_tmem(s, lane_addr, 0, c);
   tmem_st_wait();
+  // the weights staged in shared memory by these threads, for the MMAs
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -249,12 +255,12 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
   for (int L = 0; L < 4; ++L) {
     if (r == 0) {
       tc_fence_after();
-      const uint32_t ahi = smem_u32(s.a_hi), alo = smem_u32(s.a_lo);
-      // accumulating onto the bias; the low parts subtracted
+      // A from tensor memory (8 columns a K block), accumulating onto the
+      // bias; the low parts subtracted
       if (L == 0) {
         const uint64_t b = tc_desc(smem_u32(s.w + TC_W1), 128, 256);
-        tc_mma(tmem, tc_desc(alo, 128, 256), b, tc_idesc(128, 64) | TC_NEG_A, 1u);
-        tc_mma(tmem, tc_desc(ahi, 128, 256), b, tc_idesc(128, 64), 1u);
+        tc_mma_ta(tmem, tmem + TC_A_LO, b, tc_idesc(128, 64) | TC_NEG_A, 1u);
+        tc_mma_ta(tmem, tmem + TC_A_HI, b, tc_idesc(128, 64), 1u);
       } else {
         const int wo = L == 1 ? TC_W2 : (L == 2 ? TC_W3 : TC_W4);
         const uint32_t id = tc_idesc(128, L == 3 ? 16 : 64);
@@ -262,8 +268,8 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
           const uint64_t b = tc_desc(wb + 256u * kb, 128, 1024);
-          tc_mma(tmem, tc_desc(alo + 256u * kb, 128, 1024), b, id | TC_NEG_A, 1u);
-          tc_mma(tmem, tc_desc(ahi + 256u * kb, 128, 1024), b, id, 1u);
+          tc_mma_ta(tmem, tmem + TC_A_LO + 8u * kb, b, id | TC_NEG_A, 1u);
+          tc_mma_ta(tmem, tmem + TC_A_HI + 8u * kb, b, id, 1u);
         }
       }
       tc_commit(mbar);
@@ -286,16 +292,9 @@ __device__ __forceinline__ bool mlp_cta_tc(TcSmem& s, uint32_t tmem, uint32_t& p
         if (L < 2 || c == 0) bias_to_tmem(s, lane_addr, L + 1, c);
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], tanh_approx(v[j]), v[j]);
-        uint4 hi, lo;
-        split8(v, &hi, &lo);
-        *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 16 * c, 64)]) = hi;
-        *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 16 * c, 64)]) = lo;
-        split8(v + 8, &hi, &lo);
-        *reinterpret_cast<uint4*>(&s.a_hi[tc_off(r, 16 * c + 8, 64)]) = hi;
-        *reinterpret_cast<uint4*>(&s.a_lo[tc_off(r, 16 * c + 8, 64)]) = lo;
+        a_to_tmem(lane_addr, 8u * c, v);
       }
       tmem_st_wait();
-      fence_async_smem();
       tc_fence_before();
       __syncthreads();
     } else {

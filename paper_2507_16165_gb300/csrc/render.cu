@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(512, kMinBlocks<R>) k_coherent(const __grid_co
 // psi0 + pi first (u b from the MLP gives the crossing radius).  The rays it
 // does not answer go to a list that the FP32 integrator's list pass
 // finishes after this pass.
-// 128-thread CTAs, four per SM (54 KB of shared memory and 64 tensor-memory
+// 128-thread CTAs, four per SM (54 KB of shared memory and 128 tensor-memory
 // columns each), at most 112 registers a thread: the four CTAs (57,344
 // registers) and the FP64 band pass's four 64-register warps (8,192) fill
 // an SM's 65,536 together, so the band pass runs beside this pass.  A layer
