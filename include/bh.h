@@ -60,7 +60,7 @@ extern "C" {
 #define BH_E_DEVICE (-4)       /* device status word: watchdog / abort    */
 #define BH_E_NO_SURROGATE (-5) /* surrogate mode without trained weights  */
 #define BH_E_IO (-6)           /* file read/write failed or corrupt       */
-#define BH_E_UNSUPPORTED (-7)  /* option not available in this build      */
+#define BH_E_UNSUPPORTED (-7)  /* option or mode this entry point lacks   */
 
 /* ---- precision modes ------------------------------------------------- */
 #define BH_MODE_FP64 0      /* FP64 everywhere                              */
