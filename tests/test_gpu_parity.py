@@ -45,6 +45,9 @@ CASES = {
     "c3_fp32_ragged_250x190": (_ragged(W.config3(64, "fp32"), 250, 190), "fp32"),
     "c3_mixed_256": (W.config3(256, "mixed"), "mixed"),
     "c5_batch6_fp32": (W.config5(6, scale=16), "fp32"),
+    # several cameras in one mixed render: one band list over all their rows
+    "c5_batch6_mixed": (W.config5(6, scale=16), "mixed"),
+    "c5_batch6_fp64": (W.config5(6, scale=16), "fp64"),
 }
 
 
